@@ -1,0 +1,320 @@
+"""Benchmark: DOF-stage updates/s of the fused RKDG jump-filter stage kernel.
+
+Workload: 2D Euler, gamma = 1.4, 2048 x 2048 cells on [0,1]^2, Q2 tensor-product Legendre DG (36
+DOFs per cell, 151 M DOFs), LLF flux, SSP-RK3, jump filter after every stage, outflow boundaries,
+seeded four-quadrant Riemann data projected on the GPU. One benchmark step = one SSP-RK3 step over
+the whole mesh = 3 stage launches = 3 x 151 M DOF-stage updates.
+
+Headline `value`: the FP32 form (FP32 stage arithmetic, cell averages in double-float), inputs
+resident in HBM. Beside it: the plain FP64 path, the end-to-end figure through the C ABI with host
+buffers, the roofline of the stage kernel, GPU clocks during the timed region, and the FP64 CPU
+oracle timed on this host's cores. `--impl reference` times that oracle alone (the reference arm).
+
+Contract: python bench.py --gpus N --steps K --warmup W; for N > 1 launched by torch.distributed.run,
+one rank per GPU (replicas: every rank solves its own copy, no data-path collective).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "euler2d_q2_2048x2048_quadrant_riemann"
+METRIC = "2D Euler P2 DOF-stage updates/s (FP32 vs FP64) + served-solve p50/p99 latency"
+UNIT = "DOF-stage/s"
+QUADRANT_SEED_FILE = os.path.join(ROOT, "tests", "golden", "quadrant_seeds.txt")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def first_accepted_seed():
+    try:
+        with open(QUADRANT_SEED_FILE) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                s, ok, _ = line.split()
+                if int(ok):
+                    return int(s)
+    except OSError:
+        pass
+    return 1
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.samples = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(p[1]) for p in self.samples if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in self.samples if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in self.samples for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_solver(N, precision, nx, seed, stream):
+    from paper_2407_19169_gb300 import inputs as I
+    s = N.Solver(dim=2, nx=nx, ny=nx, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(N.BC_OUTFLOW,) * 4, k=2,
+                 eq=N.EQ_EULER, filter=1, cfl=0.1, gamma=1.4, precision=precision, stream=stream)
+    s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(seed))
+    return s
+
+
+def time_steps(torch, s, steps, stream, barrier):
+    """K steps bracketed by a barrier and synchronize on both sides, CUDA events on the solver's
+    stream. Returns (ms, kernel launches inside the timed region)."""
+    barrier()
+    torch.cuda.synchronize()
+    l0 = s.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance_steps(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    st, t, n = s.sync()
+    if st != 0:
+        raise RuntimeError("solver reported status %d during the timed steps" % st)
+    return e0.elapsed_time(e1), s.kernel_launches() - l0
+
+
+def cpu_baseline(nx_sample, seconds, seed):
+    """The FP64 oracle (as it stands) on this host's cores, on the same problem at a bounded size."""
+    import oracle as O
+    from paper_2407_19169_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    p = O.Problem(dim=2, nx=nx_sample, ny=nx_sample, x0=0, x1=1, y0=0, y1=1, k=2, eq=O.EQ_EULER,
+                  bc=(O.BC_OUTFLOW,) * 4, cfl=0.1)
+    u = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(seed))
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        u = O.step(p, u, O.dt(p, u))
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and steps >= 2:
+            break
+    dofs = p.ncell * p.nvars * p.nmodes
+    return {"value": 3.0 * dofs * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%dx%d Q2 Euler quadrant problem, %d SSP-RK3 steps (%.1f s), FP64, %d threads"
+                      % (nx_sample, nx_sample, steps, el, cores)}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, each step a bounded sample (one SSP-RK3
+    step of the same problem on a 256 x 256 mesh)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2407_19169_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    nxs = 256
+    p = O.Problem(dim=2, nx=nxs, ny=nxs, x0=0, x1=1, y0=0, y1=1, k=2, eq=O.EQ_EULER,
+                  bc=(O.BC_OUTFLOW,) * 4, cfl=0.1)
+    seed = first_accepted_seed()
+    u = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(seed))
+    for _ in range(args.warmup):
+        u = O.step(p, u, O.dt(p, u))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = O.step(p, u, O.dt(p, u))
+    el = time.perf_counter() - t0
+    dofs = p.ncell * p.nvars * p.nmodes
+    value = 3.0 * dofs * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_step": "one SSP-RK3 step on a 256x256 mesh of "
+                       "the same problem (bounded sample)", "seed": seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "256x256 Q2 Euler quadrant problem, %d steps, %d threads"
+                                       % (args.steps, cores)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mesh", type=int, default=2048, help="cells per side (2048 = the benchmark workload)")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.mesh == 2048:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2407_19169_gb300 import _native as N
+    if not os.path.exists(N.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    seed = first_accepted_seed()
+    nx = args.mesh
+    out = {}
+
+    # ---- headline: the FP32 form, inputs resident ----
+    s32 = make_solver(N, N.PREC_FP32_MIXED, nx, seed, sh)
+    nv, nm, nc = s32.shape
+    ndof = nv * nm * nc
+    s32.advance_steps(args.warmup)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms32, launches32 = time_steps(torch, s32, args.steps, stream, barrier)
+    clocks = clk.summary()
+    state_bytes32 = nv * nc * (8 + 4 * (nm - 1))
+
+    # ---- the plain FP64 path ----
+    fp64 = None
+    if not args.skip_fp64:
+        s64 = make_solver(N, N.PREC_FP64, nx, seed, sh)
+        s64.advance_steps(args.warmup)
+        torch.cuda.synchronize()
+        ms64, launches64 = time_steps(torch, s64, args.steps, stream, barrier)
+        fp64 = {"value": 3.0 * ndof * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                "stage_kernel_ms": ms64 / (3 * args.steps), "dtype": "f64"}
+        s64.close()
+        del s64
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty(ndof, dtype=torch.float64, pin_memory=True)
+        s32.read_state_host_ptr(host.data_ptr(), ndof)          # a valid initial state
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s32.write_state_host_ptr(host.data_ptr(), ndof, 0.0)
+        s32.advance_steps(args.steps)
+        s32.read_state_host_ptr(host.data_ptr(), ndof)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": 3.0 * ndof * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * ndof / args.steps), "d2h_bytes_per_step": int(8 * ndof / args.steps),
+               "note": "one solve of K steps per timed region: the FP64 canonical state is copied in "
+                       "from pinned host memory before the steps and read back after them"}
+    s32.close()
+
+    # ---- roofline of the stage kernel (the only kernel in the timed region) ----
+    hbm, src = peaks()
+    launch_ms = ms32 / (3 * args.steps)
+    alg_bytes = (8.0 / 3.0) * state_bytes32          # 8 state moves per 3 stages
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    value = 3.0 * ndof * args.steps / (ms32 * 1e-3)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms32], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        value = world * 3.0 * ndof * args.steps / (ms_max * 1e-3)
+        ms32 = ms_max
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": [nx, nx], "degree": 2, "basis": "Q2", "dofs": ndof,
+                   "seed": seed, "precision": "FP32 stage arithmetic, cell averages double-float",
+                   "l2": "inputs larger than L2 (state %.0f MB per buffer)" % (state_bytes32 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_source": src,
+                     "kernel": "stage2d_kernel<2,EULER,Q,FP32 form>", "launch_ms": launch_ms,
+                     "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+        "gpu_launches": launches32,
+        "fp64": fp64,
+        "e2e": e2e,
+    }
+    if not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(128 if nx >= 128 else nx, args.cpu_seconds, seed)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

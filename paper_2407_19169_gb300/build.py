@@ -1,0 +1,68 @@
+"""Build the CUDA library libdgjf.so (sm_103a) in-tree.
+
+Each translation unit is compiled by its own nvcc process, in parallel, then linked with
+`nvcc -shared`. Nothing here falls back to a CPU implementation: without nvcc the build fails.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libdgjf.so")
+UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+         "-Xcompiler", "-fvisibility=hidden"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA library cannot be built")
+
+
+def _deps():
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + \
+        [os.path.join(os.path.dirname(HERE), "include", "dg.h")]
+
+
+def _stale(obj: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(d) > t for d in _deps())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    jobs = []
+    for u in UNITS:
+        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
+        if force or _stale(obj):
+            cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, u), "-o", obj]
+            jobs.append((u, cmd))
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): u for u, cmd in jobs}
+            for f in cf.as_completed(futs):
+                r = f.result()
+                if r.returncode != 0:
+                    raise RuntimeError("nvcc failed for %s:\n%s" % (futs[f], r.stderr[-4000:]))
+                if verbose and r.stderr:
+                    print(r.stderr)
+    objs = [os.path.join(BUILD, u.replace(".cu", ".o")) for u in UNITS]
+    if jobs or not os.path.exists(LIB):
+        tmp = LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,310 @@
+// dg_device.cuh — device building blocks of the RKDG jump-filter kernels (sm_103a).
+//
+// Basis (Eq. GLbasisequation): Legendre P_l on [-1,1], tabulated at compile time from
+// dg_tables.cuh; endpoint derivatives from the closed form
+//   P_l^{(r)}(+1) = (l+r)! / (2^r r! (l-r)!),   P_l^{(r)}(-1) = (-1)^{l+r} P_l^{(r)}(+1).
+// Physics: Burgers f = u^2/2, linear advection f = a u, Euler (Section 3.1, 3.2) with
+// p = (gamma-1)(E - |m|^2/(2 rho)), wave speed |u_n| + c, enthalpy H = (E + p)/rho.
+// Numerical flux: local Lax–Friedrichs (Section 3).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_tables.cuh"
+
+namespace dgk {
+
+enum { EQ_ADV = 0, EQ_BURG = 1, EQ_EULER = 2 };
+enum { BASIS_Q = 0, BASIS_P = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+
+// Error bits of DevScalars::err.
+enum : unsigned { ERRB_NONPHYS = 1u, ERRB_RATE = 2u };
+
+// Device-resident step control shared by the stage kernels of one solver.
+struct DevScalars {
+  double t;                       // current time
+  double T_end;                   // stop time (inf for unclipped stepping)
+  double dt;                      // step size of the step in progress (written by stage 0)
+  unsigned long long rate_bits[2];  // CFL rate max (bits of a non-negative double), by step parity
+  long long step;                 // completed steps
+  long long max_step;             // stop when step reaches this
+  unsigned int done;              // 1: t >= T_end or step >= max_step; stage kernels do nothing
+  unsigned int err;               // ERRB_* bits; stage kernels do nothing
+  unsigned int blocks_done;       // last-block counter of the final stage
+  unsigned int is_last;           // current step is clipped to land on T_end
+};
+
+__host__ __device__ constexpr double cfact(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+// d^r P_l at -1 (side 0) or +1 (side 1), closed form.
+__host__ __device__ constexpr double dend(int side, int l, int r) {
+  return r > l ? 0.0
+               : ((side == 0 && ((l + r) & 1)) ? -1.0 : 1.0) * cfact(l + r) /
+                     (double)(1 << r) / cfact(r) / cfact(l - r);
+}
+
+// Mode enumeration: q outer, p inner; P^k drops p + q > k.
+template <int K, int BASIS>
+struct Modes {
+  static constexpr int NM = BASIS == BASIS_Q ? (K + 1) * (K + 1) : (K + 1) * (K + 2) / 2;
+  static constexpr int LMAX = BASIS == BASIS_Q ? 2 * K : K;
+  __host__ __device__ static constexpr int p(int m) {
+    if (BASIS == BASIS_Q) return m % (K + 1);
+    int idx = 0;
+    for (int q = 0; q <= K; ++q)
+      for (int pp = 0; pp + q <= K; ++pp) {
+        if (idx == m) return pp;
+        ++idx;
+      }
+    return -1;
+  }
+  __host__ __device__ static constexpr int q(int m) {
+    if (BASIS == BASIS_Q) return m / (K + 1);
+    int idx = 0;
+    for (int qq = 0; qq <= K; ++qq)
+      for (int pp = 0; pp + qq <= K; ++pp) {
+        if (idx == m) return qq;
+        ++idx;
+      }
+    return -1;
+  }
+  // Multi-indices alpha = (a1, a2) with nonzero derivatives: a1, a2 <= K (and a1 + a2 <= K for P^k).
+  static constexpr int NA = BASIS == BASIS_Q ? (K + 1) * (K + 1) : (K + 1) * (K + 2) / 2;
+  __host__ __device__ static constexpr int a1(int a) { return p(a); }
+  __host__ __device__ static constexpr int a2(int a) { return q(a); }
+};
+
+// Small constexpr array usable in device code (tables are built by the compiler front end and the
+// unrolled loops read them at constant indices).
+template <class V, int N>
+struct carr {
+  V v[N];
+  __host__ __device__ constexpr V operator[](int i) const { return v[i]; }
+  __host__ __device__ constexpr V& operator[](int i) { return v[i]; }
+};
+
+template <int EQ, int DIM>
+struct NVars {
+  static constexpr int value = EQ == EQ_EULER ? (DIM == 1 ? 3 : 4) : 1;
+};
+
+// Physical constants handed to the kernels.
+struct PhysConst {
+  double gamma, ax, ay;
+};
+
+// ---- fluxes ------------------------------------------------------------------------------
+// 1D flux of u (NV = 1 or 3).
+template <int EQ, class T>
+__device__ __forceinline__ void flux1d(const T* u, T* f, T gm1, T ax) {
+  if constexpr (EQ == EQ_ADV) {
+    f[0] = ax * u[0];
+  } else if constexpr (EQ == EQ_BURG) {
+    f[0] = T(0.5) * u[0] * u[0];
+  } else {
+    T vel = u[1] / u[0];
+    T p = gm1 * (u[2] - T(0.5) * u[1] * vel);
+    f[0] = u[1];
+    f[1] = u[1] * vel + p;
+    f[2] = vel * (u[2] + p);
+  }
+}
+
+template <int EQ, class T>
+__device__ __forceinline__ T speed1d(const T* u, T gamma, T gm1, T ax) {
+  if constexpr (EQ == EQ_ADV) {
+    return fabs(ax);
+  } else if constexpr (EQ == EQ_BURG) {
+    return fabs(u[0]);
+  } else {
+    T vel = u[1] / u[0];
+    T p = gm1 * (u[2] - T(0.5) * u[1] * vel);
+    return fabs(vel) + sqrt(gamma * p / u[0]);
+  }
+}
+
+// 2D flux in direction DIR (0 = x, 1 = y).
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void flux2d(const T* u, T* f, T gm1, T ax, T ay) {
+  if constexpr (EQ == EQ_ADV) {
+    f[0] = (DIR == 0 ? ax : ay) * u[0];
+  } else if constexpr (EQ == EQ_BURG) {
+    f[0] = T(0.5) * u[0] * u[0];
+  } else {
+    T inv = T(1) / u[0];
+    T vx = u[1] * inv, vy = u[2] * inv;
+    T p = gm1 * (u[3] - T(0.5) * (u[1] * vx + u[2] * vy));
+    T vn = DIR == 0 ? vx : vy;
+    f[0] = u[0] * vn;
+    f[1] = u[1] * vn + (DIR == 0 ? p : T(0));
+    f[2] = u[2] * vn + (DIR == 1 ? p : T(0));
+    f[3] = vn * (u[3] + p);
+  }
+}
+
+// Both directional fluxes at a volume point (shares the primitive variables).
+template <int EQ, class T>
+__device__ __forceinline__ void flux2d_xy(const T* u, T* fx, T* fy, T gm1, T ax, T ay) {
+  if constexpr (EQ == EQ_ADV) {
+    fx[0] = ax * u[0];
+    fy[0] = ay * u[0];
+  } else if constexpr (EQ == EQ_BURG) {
+    fx[0] = T(0.5) * u[0] * u[0];
+    fy[0] = fx[0];
+  } else {
+    T inv = T(1) / u[0];
+    T vx = u[1] * inv, vy = u[2] * inv;
+    T p = gm1 * (u[3] - T(0.5) * (u[1] * vx + u[2] * vy));
+    T ep = u[3] + p;
+    fx[0] = u[1];
+    fx[1] = u[1] * vx + p;
+    fx[2] = u[2] * vx;
+    fx[3] = vx * ep;
+    fy[0] = u[2];
+    fy[1] = u[1] * vy;
+    fy[2] = u[2] * vy + p;
+    fy[3] = vy * ep;
+  }
+}
+
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ T speed2d(const T* u, T gamma, T gm1, T ax, T ay) {
+  if constexpr (EQ == EQ_ADV) {
+    return fabs(DIR == 0 ? ax : ay);
+  } else if constexpr (EQ == EQ_BURG) {
+    return fabs(u[0]);
+  } else {
+    T inv = T(1) / u[0];
+    T vx = u[1] * inv, vy = u[2] * inv;
+    T p = gm1 * (u[3] - T(0.5) * (u[1] * vx + u[2] * vy));
+    return fabs(DIR == 0 ? vx : vy) + sqrt(gamma * p * inv);
+  }
+}
+
+// max that keeps a NaN: a non-physical trace (p < 0 gives a NaN sound speed) must reach the cell
+// averages and be reported, not be hidden by the other side's wave speed.
+template <class T>
+__device__ __forceinline__ T nan_max(T a, T b) {
+  return (a > b || a != a) ? a : b;
+}
+
+// Local Lax–Friedrichs flux for a 1D face: fh = 1/2 (f(uL) + f(uR)) - 1/2 alpha (uR - uL).
+template <int EQ, class T>
+__device__ __forceinline__ void llf1d(const T* uL, const T* uR, T* fh, T gamma, T gm1, T ax) {
+  constexpr int NV = EQ == EQ_EULER ? 3 : 1;
+  T fL[NV], fR[NV];
+  flux1d<EQ>(uL, fL, gm1, ax);
+  flux1d<EQ>(uR, fR, gm1, ax);
+  T a = nan_max(speed1d<EQ>(uL, gamma, gm1, ax), speed1d<EQ>(uR, gamma, gm1, ax));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) fh[v] = T(0.5) * (fL[v] + fR[v]) - T(0.5) * a * (uR[v] - uL[v]);
+}
+
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void llf2d(const T* uL, const T* uR, T* fh, T gamma, T gm1, T ax, T ay) {
+  constexpr int NV = EQ == EQ_EULER ? 4 : 1;
+  T fL[NV], fR[NV];
+  flux2d<EQ, DIR>(uL, fL, gm1, ax, ay);
+  flux2d<EQ, DIR>(uR, fR, gm1, ax, ay);
+  T a = nan_max(speed2d<EQ, DIR>(uL, gamma, gm1, ax, ay), speed2d<EQ, DIR>(uR, gamma, gm1, ax, ay));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) fh[v] = T(0.5) * (fL[v] + fR[v]) - T(0.5) * a * (uR[v] - uL[v]);
+}
+
+// Cell-average quantities for the filter and the CFL rate: beta^x, beta^y, 1/Hbar.
+template <int EQ, int DIM, class T>
+__device__ __forceinline__ void avg_params(const T* ub, T gamma, T gm1, T ax, T ay, T& bx, T& by,
+                                           T& invH, bool& physical) {
+  if constexpr (EQ == EQ_ADV) {
+    bx = fabs(ax);
+    by = fabs(ay);
+    invH = T(1);
+    physical = isfinite(ub[0]);
+  } else if constexpr (EQ == EQ_BURG) {
+    bx = fabs(ub[0]);
+    by = bx;
+    invH = T(1);
+    physical = isfinite(ub[0]);
+  } else if constexpr (DIM == 1) {
+    T vel = ub[1] / ub[0];
+    T p = gm1 * (ub[2] - T(0.5) * ub[1] * vel);
+    T c = sqrt(gamma * p / ub[0]);
+    bx = fabs(vel) + c;
+    by = T(0);
+    invH = ub[0] / (ub[2] + p);
+    physical = (ub[0] > T(0)) && (p > T(0)) && isfinite(bx) && isfinite(invH);
+  } else {
+    T inv = T(1) / ub[0];
+    T vx = ub[1] * inv, vy = ub[2] * inv;
+    T p = gm1 * (ub[3] - T(0.5) * (ub[1] * vx + ub[2] * vy));
+    T c = sqrt(gamma * p * inv);
+    bx = fabs(vx) + c;
+    by = fabs(vy) + c;
+    invH = ub[0] / (ub[3] + p);
+    physical = (ub[0] > T(0)) && (p > T(0)) && isfinite(bx) && isfinite(by) && isfinite(invH);
+  }
+}
+
+// ---- double-float arithmetic (error-free transformations; Dekker / Knuth) -------------------
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  df t = df_two_sum(a.lo, b.lo);
+  float c = __fadd_rn(s.lo, t.hi);
+  df v = df_fast_two_sum(s.hi, c);
+  float w = __fadd_rn(t.lo, v.lo);
+  return df_fast_two_sum(v.hi, w);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+__host__ __device__ inline df df_from_double(double x) {
+  float hi = (float)x;
+  float lo = (float)(x - (double)hi);
+  return {hi, lo};
+}
+
+// Atomic max of a non-negative double through its bit pattern (monotone for x >= 0; NaN sorts
+// above +inf, so a NaN rate is kept and reported).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double x) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(x));
+}
+
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = (y > x || y != y) ? y : x;
+  }
+  return x;
+}
+
+}  // namespace dgk

@@ -1,0 +1,43 @@
+// dg_internal.h — host-side pieces shared by the C-ABI implementation and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "dg_device.cuh"
+
+namespace dgk {
+
+enum { PREC_F64 = 0, PREC_F32M = 1 };
+
+// Type-erased launcher of one stage-kernel instantiation.
+struct StageLauncher {
+  // launch(args, grid, block, dynamic smem bytes, stream)
+  cudaError_t (*launch)(const void* args, unsigned grid, unsigned block, size_t smem, cudaStream_t s);
+  cudaError_t (*set_smem)(size_t bytes);  // raise the dynamic shared-memory limit
+  size_t slot_bytes_per_warp;             // 2D: per-warp row slots; 1D: 0
+};
+
+// Instantiation tables (one per kernel file). Return {nullptr} if the combination is not compiled.
+StageLauncher stage1d_launcher(int K, int EQ, int PREC);
+StageLauncher stage2d_f64_launcher(int K, int EQ, int BASIS);
+StageLauncher stage2d_f32_launcher(int K, int EQ, int BASIS);
+
+// Geometry and physics of one solver, as the auxiliary kernels see it.
+struct AuxGeom {
+  int dim, nx, ny, k, nv, nm, basis, eq, prec;
+  long long ncell;
+  double x0, y0, hx, hy, gamma, ax, ay;
+  int mp[16], mq[16];  // (p, q) of each mode
+};
+
+cudaError_t aux_init_tables();  // copy Gauss rules to constant memory of the current device
+cudaError_t launch_project(const AuxGeom& g, int ic, const double* prm, int nprm, int nq,
+                           double* canon_out, cudaStream_t s);
+cudaError_t launch_rate(const AuxGeom& g, const void* state, DevScalars* sc, int slot, cudaStream_t s);
+cudaError_t launch_to_storage(const AuxGeom& g, const double* canon, void* state, cudaStream_t s);
+cudaError_t launch_from_storage(const AuxGeom& g, const void* state, double* canon, cudaStream_t s);
+cudaError_t launch_mass(const AuxGeom& g, const void* state, double* partials, double* out, cudaStream_t s);
+size_t state_bytes(const AuxGeom& g);
+constexpr int MASS_BLOCKS = 256;
+
+}  // namespace dgk

@@ -1,0 +1,218 @@
+// stage1d.cuh — fused 1D SSP-RK3 stage with the jump filter (one launch per stage).
+//
+// Per cell K_j (Section 2.1):
+//   R^l = (2l+1)/h [ sum_q w_q f(u_h(xi_q)) P_l'(xi_q) - f^_{j+1/2} + (-1)^l f^_{j-1/2} ]   (Eq. scheme:DG)
+//   u~ = c0 u^n + c1 (u^(s) + dt R)                                                          (Eq. rkdg1)
+//   u^l <- exp(-sigma^l dt) u~^l,  sigma^l = beta/(h Hbar) max_v (J_0 + sum_{m=1..l} m(m+1) h^m J_m)
+// the last line being Eqs. (para:damp2)-(para:damp21) with c_f^l = beta/(4 l(l+1)) (1/Hbar for
+// Euler, Section 3.1) substituted, the max over components of Eq. (para:dampsystems1d), and
+// J_m = |[d^m u]_{j-1/2}| + |[d^m u]_{j+1/2}| with physical derivatives.
+//
+// Parallel structure: a warp owns 32 consecutive cells and writes the middle 28 (2-cell halo per
+// side); traces, face fluxes, end derivatives and face jumps move between lanes by shuffles. Each
+// face flux and face jump is computed once, by the face's left cell.
+#pragma once
+#include "stage2d.cuh"
+
+namespace dgk {
+
+struct Stage1DArgs {
+  const void* uin;
+  const void* un;
+  void* uout;
+  int nx;
+  long long ncell;
+  double h;
+  int bc;            // BC_PERIODIC or BC_OUTFLOW (both ends alike)
+  double c0, c1;
+  int stage;
+  int filter_on;
+  double gamma, ax, cfl;
+  int nwarps;
+  DevScalars* sc;
+};
+
+template <int K, int EQ, class PR>
+struct Stage1D {
+  using T = typename PR::T;
+  static constexpr int NM = K + 1;
+  static constexpr int NV = NVars<EQ, 1>::value;
+  static constexpr int NQ = K + 1;
+  using GR = GaussRule<NQ>;
+  using ST = Store<PR, NV, NM>;
+
+  static __device__ __forceinline__ T sd(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
+  static __device__ __forceinline__ T su(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
+
+  static __device__ void run(const Stage1DArgs& a, unsigned char* smem) {
+    const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
+    if (!ctl.run) return;
+    const T dt = (T)ctl.dt;
+    const int lane = threadIdx.x & 31;
+    double* red = (double*)smem;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool active = gw < a.nwarps;
+    const int nx = a.nx;
+    const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax;
+    const T inv_h = (T)(1.0 / a.h), scl = (T)(2.0 / a.h);
+    double my_rate = 0.0;
+    bool my_ok = true;
+    if (active) {
+      const int x = (int)gw * STRIP_OUT - 2 + lane;
+      const bool per = a.bc == BC_PERIODIC;
+      const int xc = per ? ((x % nx) + nx) % nx : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
+      const bool lbnd = !per && x == 0, rbnd = !per && x == nx - 1;
+      const bool out_lane = lane >= 2 && lane < 2 + STRIP_OUT && x >= 0 && x < nx;
+      T u[NV][NM], lo0[NV];
+      ST::load(a.uin, a.ncell, xc, u, lo0);
+      // traces at xi = -1 and +1
+      T tl[NV], tr[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T sl = T(0), sr = T(0);
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+          sr += u[v][l];
+          sl += (l & 1) ? -u[v][l] : u[v][l];
+        }
+        tl[v] = sl;
+        tr[v] = sr;
+      }
+      // face fluxes: right face by this lane, left face from the left lane
+      T nb[NV], FR[NV], FL[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) nb[v] = sd(tl[v], 1);
+      if (rbnd) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) nb[v] = tr[v];
+      }
+      llf1d<EQ>(tr, nb, FR, gam, gm1, ax);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) FL[v] = su(FR[v], 1);
+      if (lbnd) llf1d<EQ>(tl, tl, FL, gam, gm1, ax);
+      // volume integral
+      T acc[NV][NM];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int l = 0; l < NM; ++l) acc[v][l] = T(0);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        T uq[NV], fq[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T s = T(0);
+#pragma unroll
+          for (int l = 0; l < NM; ++l) s += u[v][l] * (T)GR::P(l, q);
+          uq[v] = s;
+        }
+        flux1d<EQ>(uq, fq, gm1, ax);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int l = 1; l < NM; ++l) acc[v][l] += fq[v] * (T)(GR::w(q) * GR::dP(l, q));
+      }
+      T un_[NV][NM], unlo[NV];
+      if (a.stage > 0) ST::load(a.un, a.ncell, xc, un_, unlo);
+      T ut[NV][NM], ulo[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+          const T R = (T)(2 * l + 1) * inv_h * (acc[v][l] - FR[v] + ((l & 1) ? -FL[v] : FL[v]));
+          if (PR::MIXED && l == 0) continue;
+          T val = (T)a.c1 * (u[v][l] + dt * R);
+          if (a.stage > 0) val += (T)a.c0 * un_[v][l];
+          ut[v][l] = val;
+        }
+        ulo[v] = T(0);
+        if constexpr (PR::MIXED) {
+          // cell average in double-float: c1 u0 + c1 dt/h (F_L - F_R) + c0 un0
+          const df cf = df_from_double(a.c1 * ctl.dt / a.h);
+          df m0 = df_mul(df_from_double(a.c1), df{u[v][0], lo0[v]});
+          m0 = df_add(m0, df_mul_f(cf, FL[v]));
+          m0 = df_add(m0, df_mul_f(cf, -FR[v]));
+          if (a.stage > 0) m0 = df_add(m0, df_mul(df_from_double(a.c0), df{un_[v][0], unlo[v]}));
+          ut[v][0] = m0.hi;
+          ulo[v] = m0.lo;
+        }
+      }
+      T ub[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ub[v] = ut[v][0];
+      T bx, by, invH;
+      bool phys;
+      avg_params<EQ, 1>(ub, gam, gm1, ax, ax, bx, by, invH, phys);
+      if (a.filter_on) {
+        // end derivatives d^r u~ at xi = -1, +1 and the jump at the right face
+        T J[NV][NM];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T jr[NM];
+#pragma unroll
+          for (int r = 0; r < NM; ++r) {
+            T dl = T(0), dr = T(0);
+#pragma unroll
+            for (int l = r; l < NM; ++l) {
+              dl += ut[v][l] * (T)dend(0, l, r);
+              dr += ut[v][l] * (T)dend(1, l, r);
+            }
+            T f = T(1);
+#pragma unroll
+            for (int i = 0; i < r; ++i) f *= scl;
+            dl *= f;
+            dr *= f;
+            const T nbl = sd(dl, 1);
+            jr[r] = rbnd ? T(0) : fabs(nbl - dr);
+          }
+#pragma unroll
+          for (int r = 0; r < NM; ++r) {
+            T jl = su(jr[r], 1);
+            if (lbnd) jl = T(0);
+            J[v][r] = jl + jr[r];
+          }
+        }
+        // sigma^l = beta / (h Hbar) max_v (J_0 + sum_{m<=l} m(m+1) h^m J_m)
+        T wpow[NM];
+        {
+          double hp = 1.0;
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            wpow[m] = (T)(m == 0 ? 1.0 : m * (m + 1) * hp);
+            hp *= a.h;
+          }
+        }
+        T run[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) run[v] = J[v][0];
+#pragma unroll
+        for (int l = 1; l < NM; ++l) {
+          T best = T(0);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            run[v] += wpow[l] * J[v][l];
+            best = (run[v] > best || run[v] != run[v]) ? run[v] : best;
+          }
+          const T fac = exp(-(bx * inv_h * invH * best) * dt);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) ut[v][l] *= fac;
+        }
+      }
+      if (out_lane) {
+        ST::store(a.uout, a.ncell, xc, ut, ulo);
+        if (!phys) my_ok = false;
+        const double r = (double)bx / a.h;
+        my_rate = (r > my_rate || r != r) ? r : my_rate;
+      }
+    }
+    stage_end(a.sc, a.stage, my_rate, my_ok, red);
+  }
+};
+
+template <int K, int EQ, class PR>
+__global__ void __launch_bounds__(256) stage1d_kernel(const Stage1DArgs a) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Stage1D<K, EQ, PR>::run(a, dyn_smem);
+}
+
+}  // namespace dgk
