@@ -1,0 +1,92 @@
+"""The FP32 form (FP32 stage arithmetic, cell averages as double-float) against the FP64 oracle.
+
+Bars: relative L1 <= 1e-5 on smooth runs; on shock runs the L1 error against the exact solution
+within 2% of the FP64 path's error; mass conserved to double-float roundoff.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_19169_gb300 import _native as N
+from paper_2407_19169_gb300 import inputs as I
+
+from _helpers import pair, rel_l1
+
+pytestmark = pytest.mark.gpu
+INF = float("inf")
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_vortex_2d_q_basis_smooth(k):
+    p, s = pair(dim=2, nx=40, ny=40, x0=0, x1=10, y0=-5, y1=5, k=k, eq="euler", bc="periodic",
+                precision=N.PREC_FP32_MIXED, tile_rows=16)
+    u0 = O.project(p, O.IC_VORTEX2D, [5.0, 0.0, 5.0, 0.0])
+    s.write_state(u0)
+    s.advance_steps(100)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 100)
+    assert rel_l1(p, ug, uo) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_entropy_wave_1d_smooth(k):
+    p, s = pair(dim=1, nx=100, k=k, eq="euler", bc="periodic", precision=N.PREC_FP32_MIXED)
+    prm = [1.0, 0.2, 2 * math.pi, 1.0, 1.0]
+    u0 = O.project(p, O.IC_ENTROPY1D, prm)
+    s.write_state(u0)
+    s.advance_steps(100)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 100)
+    assert rel_l1(p, ug, uo) <= 1e-5
+
+
+def test_burgers_1d_smooth():
+    p, s = pair(dim=1, nx=200, x0=0, x1=2, k=2, eq="burgers", bc="periodic", precision=N.PREC_FP32_MIXED)
+    u0 = O.project(p, O.IC_SINE, [0.5, 1.0, math.pi, 0.0])
+    s.write_state(u0)
+    s.advance_steps(100)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 100)
+    assert rel_l1(p, ug, uo) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_riemann_1d_shock_error_within_2_percent(k):
+    seed = 1
+    prm = I.riemann1d_params(seed)
+    errs = {}
+    for prec in (N.PREC_FP64, N.PREC_FP32_MIXED):
+        p, s = pair(dim=1, nx=400, k=k, eq="euler", bc="outflow", precision=prec)
+        s.set_initial(N.IC_RIEMANN1D, prm)
+        s.advance_to(0.1)
+        ug, t = s.read_state()
+        assert t == 0.1
+        errs[prec] = O.errors(p, ug, O.EX_RIEMANN1D, prm, 0.1, var=0)[0]
+    assert abs(errs[N.PREC_FP32_MIXED] - errs[N.PREC_FP64]) <= 0.02 * errs[N.PREC_FP64]
+
+
+def test_mass_conserved_fp32_form_2d():
+    p, s = pair(dim=2, nx=64, ny=40, x0=0, x1=1, y0=0, y1=0.625, k=2, eq="euler", bc="periodic",
+                precision=N.PREC_FP32_MIXED)
+    u0 = I.random_modal_state(p.shape, 78, I.EULER2D_AVG, high_scale=0.02)
+    s.write_state(u0)
+    m0 = s.mass()
+    s.advance_steps(200)
+    assert s.sync()[0] == 0
+    m1 = s.mass()
+    np.testing.assert_allclose(m1, m0, rtol=2e-13, atol=1e-13)
+
+
+def test_mass_conserved_fp32_form_1d():
+    p, s = pair(dim=1, nx=300, x0=0, x1=2, k=3, eq="burgers", bc="periodic", precision=N.PREC_FP32_MIXED)
+    u0 = O.project(p, O.IC_SINE, [0.5, 1.0, math.pi, 0.0])
+    s.write_state(u0)
+    m0 = s.mass()
+    s.advance_steps(500)
+    assert s.sync()[0] == 0
+    np.testing.assert_allclose(s.mass(), m0, rtol=2e-13, atol=1e-13)
