@@ -161,7 +161,7 @@ def cpu_baseline(nx_sample, seconds, seed):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores, each step a bounded sample (one SSP-RK3
-    step of the same problem on a 256 x 256 mesh)."""
+    step of the same problem on a 128 x 128 mesh)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
@@ -169,7 +169,7 @@ def run_reference(args):
     from paper_2407_19169_gb300 import inputs as I
     cores = os.cpu_count() or 1
     O.set_threads(cores)
-    nxs = 256
+    nxs = 128
     p = O.Problem(dim=2, nx=nxs, ny=nxs, x0=0, x1=1, y0=0, y1=1, k=2, eq=O.EQ_EULER,
                   bc=(O.BC_OUTFLOW,) * 4, cfl=0.1)
     seed = first_accepted_seed()
@@ -186,10 +186,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference_step": "one SSP-RK3 step on a 256x256 mesh of "
+            "config": {"workload": WORKLOAD, "reference_step": "one SSP-RK3 step on a 128x128 mesh of "
                        "the same problem (bounded sample)", "seed": seed},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "256x256 Q2 Euler quadrant problem, %d steps, %d threads"
+                             "sample": "128x128 Q2 Euler quadrant problem, %d steps, %d threads"
                                        % (args.steps, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
