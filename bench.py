@@ -231,8 +231,12 @@ def main():
     else:
         def barrier():
             pass
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the legacy default stream (handle 0) cannot hold a captured graph, and the
+    # events below must sit on the stream the kernels run on
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
+    assert sh != 0
     seed = first_accepted_seed()
     nx = args.mesh
     out = {}

@@ -118,6 +118,11 @@ static void eval_cell(const orc_problem* p, const ctx_t* c, const double* u, lon
   }
 }
 
+/* The outflow ghost cell: the constant state equal to the interior cell's average. */
+static void cell_average(const ctx_t* c, const double* u, long cell, double* val) {
+  for (int v = 0; v < c->nv; ++v) val[v] = U(u, v, 0, cell);
+}
+
 void orc_eval(const orc_problem* p, const double* u, int cell, double xi, double eta, double* val) {
   ctx_t c;
   make_ctx(p, &c);
@@ -159,9 +164,10 @@ static void residual_1d(const orc_problem* p, const ctx_t* c, const double* u, d
     eval_cell(p, c, u, i, 1.0, 0.0, own_r);
     eval_cell(p, c, u, i, -1.0, 0.0, own_l);
     long ir = neighbour(p, (int)i, 0, 0, 1), il = neighbour(p, (int)i, 0, 0, 0);
-    if (ir >= 0) eval_cell(p, c, u, ir, -1.0, 0.0, nb); else memcpy(nb, own_r, sizeof(nb));
+    /* outflow: the ghost cell holds the constant state equal to this cell's average */
+    if (ir >= 0) eval_cell(p, c, u, ir, -1.0, 0.0, nb); else cell_average(c, u, i, nb);
     llf(p, 0, own_r, nb, fr);
-    if (il >= 0) eval_cell(p, c, u, il, 1.0, 0.0, nb); else memcpy(nb, own_l, sizeof(nb));
+    if (il >= 0) eval_cell(p, c, u, il, 1.0, 0.0, nb); else cell_average(c, u, i, nb);
     llf(p, 0, nb, own_l, fl);
     for (int v = 0; v < c->nv; ++v)
       for (int l = 0; l <= c->k; ++l) {
@@ -203,7 +209,7 @@ static void residual_2d(const orc_problem* p, const ctx_t* c, const double* u, d
       double in[ORC_MAXNV], out[ORC_MAXNV], fh[ORC_MAXNV];
       /* right edge, n = (+1, 0): left state = this cell at xi=+1, right state = neighbour at xi=-1 */
       eval_cell(p, c, u, cell, 1.0, s, in);
-      if (nb_r >= 0) eval_cell(p, c, u, nb_r, -1.0, s, out); else memcpy(out, in, sizeof(out));
+      if (nb_r >= 0) eval_cell(p, c, u, nb_r, -1.0, s, out); else cell_average(c, u, cell, out);
       llf(p, 0, in, out, fh);
       for (int m = 0; m < c->nm; ++m) {
         double phi = c->Pe[1][c->mp[m]] * c->P[c->mq[m]][g];
@@ -211,7 +217,7 @@ static void residual_2d(const orc_problem* p, const ctx_t* c, const double* u, d
       }
       /* left edge, n = (-1, 0): left state = neighbour at xi=+1, right state = this cell at xi=-1 */
       eval_cell(p, c, u, cell, -1.0, s, in);
-      if (nb_l >= 0) eval_cell(p, c, u, nb_l, 1.0, s, out); else memcpy(out, in, sizeof(out));
+      if (nb_l >= 0) eval_cell(p, c, u, nb_l, 1.0, s, out); else cell_average(c, u, cell, out);
       llf(p, 0, out, in, fh);
       for (int m = 0; m < c->nm; ++m) {
         double phi = c->Pe[0][c->mp[m]] * c->P[c->mq[m]][g];
@@ -219,7 +225,7 @@ static void residual_2d(const orc_problem* p, const ctx_t* c, const double* u, d
       }
       /* top edge, n = (0, +1) */
       eval_cell(p, c, u, cell, s, 1.0, in);
-      if (nb_t >= 0) eval_cell(p, c, u, nb_t, s, -1.0, out); else memcpy(out, in, sizeof(out));
+      if (nb_t >= 0) eval_cell(p, c, u, nb_t, s, -1.0, out); else cell_average(c, u, cell, out);
       llf(p, 1, in, out, fh);
       for (int m = 0; m < c->nm; ++m) {
         double phi = c->P[c->mp[m]][g] * c->Pe[1][c->mq[m]];
@@ -227,7 +233,7 @@ static void residual_2d(const orc_problem* p, const ctx_t* c, const double* u, d
       }
       /* bottom edge, n = (0, -1) */
       eval_cell(p, c, u, cell, s, -1.0, in);
-      if (nb_b >= 0) eval_cell(p, c, u, nb_b, s, 1.0, out); else memcpy(out, in, sizeof(out));
+      if (nb_b >= 0) eval_cell(p, c, u, nb_b, s, 1.0, out); else cell_average(c, u, cell, out);
       llf(p, 1, out, in, fh);
       for (int m = 0; m < c->nm; ++m) {
         double phi = c->P[c->mp[m]][g] * c->Pe[0][c->mq[m]];
@@ -266,9 +272,12 @@ static void sigma_1d(const orc_problem* p, const ctx_t* c, const double* u, long
   for (int v = 0; v < c->nv; ++v)
     for (int r = 0; r <= c->k; ++r) {
       /* ||[d^r u]||_{dK_j} = |w(x_{j-1/2}^+) - w(x_{j-1/2}^-)| + |w(x_{j+1/2}^+) - w(x_{j+1/2}^-)| */
-      double jl = 0.0, jr = 0.0;
-      if (il >= 0) jl = fabs(end_deriv_1d(c, u, v, i, 0, r) - end_deriv_1d(c, u, v, il, 1, r));
-      if (ir >= 0) jr = fabs(end_deriv_1d(c, u, v, ir, 0, r) - end_deriv_1d(c, u, v, i, 1, r));
+      /* outflow ghost: constant state = this cell's average (value u_bar, derivatives 0) */
+      const double ghost = (r == 0) ? U(u, v, 0, i) : 0.0;
+      double dl_nb = il >= 0 ? end_deriv_1d(c, u, v, il, 1, r) : ghost;
+      double dr_nb = ir >= 0 ? end_deriv_1d(c, u, v, ir, 0, r) : ghost;
+      double jl = fabs(end_deriv_1d(c, u, v, i, 0, r) - dl_nb);
+      double jr = fabs(dr_nb - end_deriv_1d(c, u, v, i, 1, r));
       J[v][r] = jl + jr;
     }
   double ubar[ORC_MAXNV];
@@ -311,21 +320,19 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
     for (int a1 = 0; a1 <= k; ++a1)
       for (int a2 = 0; a2 <= k; ++a2) {
         double sv = 0.0, sh = 0.0;
+        /* outflow ghost: constant state = this cell's average (value u_bar, derivatives 0) */
+        const double ghost = (a1 == 0 && a2 == 0) ? U(u, v, 0, cell) : 0.0;
         for (int cy = 0; cy <= 1; ++cy) {        /* the two corners of each vertical edge */
-          if (nl >= 0)
-            sv += 0.5 * fabs(corner_deriv_2d(c, u, v, cell, 0, cy, a1, a2) -
-                             corner_deriv_2d(c, u, v, nl, 1, cy, a1, a2));
-          if (nr >= 0)
-            sv += 0.5 * fabs(corner_deriv_2d(c, u, v, nr, 0, cy, a1, a2) -
-                             corner_deriv_2d(c, u, v, cell, 1, cy, a1, a2));
+          double gl = nl >= 0 ? corner_deriv_2d(c, u, v, nl, 1, cy, a1, a2) : ghost;
+          double gr = nr >= 0 ? corner_deriv_2d(c, u, v, nr, 0, cy, a1, a2) : ghost;
+          sv += 0.5 * fabs(corner_deriv_2d(c, u, v, cell, 0, cy, a1, a2) - gl);
+          sv += 0.5 * fabs(gr - corner_deriv_2d(c, u, v, cell, 1, cy, a1, a2));
         }
         for (int cx = 0; cx <= 1; ++cx) {        /* the two corners of each horizontal edge */
-          if (nb >= 0)
-            sh += 0.5 * fabs(corner_deriv_2d(c, u, v, cell, cx, 0, a1, a2) -
-                             corner_deriv_2d(c, u, v, nb, cx, 1, a1, a2));
-          if (nt >= 0)
-            sh += 0.5 * fabs(corner_deriv_2d(c, u, v, nt, cx, 0, a1, a2) -
-                             corner_deriv_2d(c, u, v, cell, cx, 1, a1, a2));
+          double gb = nb >= 0 ? corner_deriv_2d(c, u, v, nb, cx, 1, a1, a2) : ghost;
+          double gt = nt >= 0 ? corner_deriv_2d(c, u, v, nt, cx, 0, a1, a2) : ghost;
+          sh += 0.5 * fabs(corner_deriv_2d(c, u, v, cell, cx, 0, a1, a2) - gb);
+          sh += 0.5 * fabs(gt - corner_deriv_2d(c, u, v, cell, cx, 1, a1, a2));
         }
         JV[v][a1][a2] = sv;
         JH[v][a1][a2] = sh;

@@ -10,7 +10,9 @@
 //
 // Parallel structure: a warp owns 32 consecutive cells and writes the middle 28 (2-cell halo per
 // side); traces, face fluxes, end derivatives and face jumps move between lanes by shuffles. Each
-// face flux and face jump is computed once, by the face's left cell.
+// face flux and face jump is computed once, by the face's left cell. Outflow boundaries: lanes
+// outside the mesh are ghost cells holding the constant state of the adjacent interior cell's
+// average (for the fluxes that of the stage input, for the jumps that of u~).
 #pragma once
 #include "stage2d.cuh"
 
@@ -61,10 +63,18 @@ struct Stage1D {
       const int x = (int)gw * STRIP_OUT - 2 + lane;
       const bool per = a.bc == BC_PERIODIC;
       const int xc = per ? ((x % nx) + nx) % nx : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
-      const bool lbnd = !per && x == 0, rbnd = !per && x == nx - 1;
+      // outflow: a lane left or right of the mesh is a ghost cell holding the constant state equal
+      // to the adjacent interior cell's average
+      const bool ghost = !per && (x < 0 || x >= nx);
       const bool out_lane = lane >= 2 && lane < 2 + STRIP_OUT && x >= 0 && x < nx;
       T u[NV][NM], lo0[NV];
       ST::load(a.uin, a.ncell, xc, u, lo0);
+      if (ghost) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int l = 1; l < NM; ++l) u[v][l] = T(0);
+      }
       // traces at xi = -1 and +1
       T tl[NV], tr[NV];
 #pragma unroll
@@ -82,14 +92,9 @@ struct Stage1D {
       T nb[NV], FR[NV], FL[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) nb[v] = sd(tl[v], 1);
-      if (rbnd) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) nb[v] = tr[v];
-      }
       llf1d<EQ>(tr, nb, FR, gam, gm1, ax);
 #pragma unroll
       for (int v = 0; v < NV; ++v) FL[v] = su(FR[v], 1);
-      if (lbnd) llf1d<EQ>(tl, tl, FL, gam, gm1, ax);
       // volume integral
       T acc[NV][NM];
 #pragma unroll
@@ -121,18 +126,23 @@ struct Stage1D {
         for (int l = 0; l < NM; ++l) {
           const T R = (T)(2 * l + 1) * inv_h * (acc[v][l] - FR[v] + ((l & 1) ? -FL[v] : FL[v]));
           if (PR::MIXED && l == 0) continue;
-          T val = (T)a.c1 * (u[v][l] + dt * R);
-          if (a.stage > 0) val += (T)a.c0 * un_[v][l];
+          // u~ = u + c0 (u^n - u) + c1 dt R: equal to c0 u^n + c1 (u + dt R) when c0 + c1 = 1, and
+          // it keeps that identity exact whatever the rounding of c0 and c1
+          T val = u[v][l] + (T)a.c1 * dt * R;
+          if (a.stage > 0) val += (T)a.c0 * (un_[v][l] - u[v][l]);
           ut[v][l] = val;
         }
         ulo[v] = T(0);
         if constexpr (PR::MIXED) {
-          // cell average in double-float: c1 u0 + c1 dt/h (F_L - F_R) + c0 un0
+          // cell average in double-float: u0 + c0 (un0 - u0) + c1 dt/h (F_L - F_R)
           const df cf = df_from_double(a.c1 * ctl.dt / a.h);
-          df m0 = df_mul(df_from_double(a.c1), df{u[v][0], lo0[v]});
+          df m0{u[v][0], lo0[v]};
+          if (a.stage > 0) {
+            const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
+            m0 = df_add(m0, df_mul(df_from_double(a.c0), d));
+          }
           m0 = df_add(m0, df_mul_f(cf, FL[v]));
           m0 = df_add(m0, df_mul_f(cf, -FR[v]));
-          if (a.stage > 0) m0 = df_add(m0, df_mul(df_from_double(a.c0), df{un_[v][0], unlo[v]}));
           ut[v][0] = m0.hi;
           ulo[v] = m0.lo;
         }
@@ -144,6 +154,16 @@ struct Stage1D {
       bool phys;
       avg_params<EQ, 1>(ub, gam, gm1, ax, ax, bx, by, invH, phys);
       if (a.filter_on) {
+        // ghost cells take the constant state of the adjacent interior cell's u~ average
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T from_right = sd(ut[v][0], 1), from_left = su(ut[v][0], 1);
+          if (ghost) {
+            ut[v][0] = x < 0 ? from_right : from_left;
+#pragma unroll
+            for (int l = 1; l < NM; ++l) ut[v][l] = T(0);
+          }
+        }
         // end derivatives d^r u~ at xi = -1, +1 and the jump at the right face
         T J[NV][NM];
 #pragma unroll
@@ -163,14 +183,10 @@ struct Stage1D {
             dl *= f;
             dr *= f;
             const T nbl = sd(dl, 1);
-            jr[r] = rbnd ? T(0) : fabs(nbl - dr);
+            jr[r] = fabs(nbl - dr);
           }
 #pragma unroll
-          for (int r = 0; r < NM; ++r) {
-            T jl = su(jr[r], 1);
-            if (lbnd) jl = T(0);
-            J[v][r] = jl + jr[r];
-          }
+          for (int r = 0; r < NM; ++r) J[v][r] = su(jr[r], 1) + jr[r];
         }
         // sigma^l = beta / (h Hbar) max_v (J_0 + sum_{m<=l} m(m+1) h^m J_m)
         T wpow[NM];

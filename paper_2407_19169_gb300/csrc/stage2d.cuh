@@ -263,14 +263,14 @@ struct Stage2D {
       const int x = strip * STRIP_OUT - 2 + lane;
       const bool perx = a.bcx == BC_PERIODIC, pery = a.bcy == BC_PERIODIC;
       const int xc = perx ? ((x % nx) + nx) % nx : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
-      const bool lbnd = !perx && x == 0;        // outflow face on this cell's left
-      const bool rbnd = !perx && x == nx - 1;   // outflow face on this cell's right
+      // outflow: columns and rows outside the mesh are ghost cells holding the constant state equal
+      // to the adjacent interior cell's average (stage input for the fluxes, u~ for the jumps)
+      const bool gcol = !perx && (x < 0 || x >= nx);
       const bool out_lane = lane >= 2 && lane < 2 + STRIP_OUT && x >= 0 && x < nx;
       const int yb = chunk * a.H;
       const int ye = min(yb + a.H, ny);
 
       T topPrev[NQ][NV];
-      bool prevRow = false;                 // row t-1 exists
       T AVprev[NV][LMAX + 1], AHbotPrev[NV][LMAX + 1];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
@@ -283,19 +283,16 @@ struct Stage2D {
 
 #pragma unroll 1
       for (int t = yb - 2; t <= ye + 1; ++t) {
-        const bool rowv = pery || (t >= 0 && t < ny);
+        const bool grow = !pery && (t < 0 || t >= ny);
         const int ty = pery ? ((t % ny) + ny) % ny : (t < 0 ? 0 : (t >= ny ? ny - 1 : t));
         const long long cell = (long long)ty * nx + xc;
         T u[NV][NM], lo0[NV];
-        if (rowv) {
-          ST::load(a.uin, a.ncell, cell, u, lo0);
-        } else {
+        ST::load(a.uin, a.ncell, cell, u, lo0);
+        if (grow || gcol) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            lo0[v] = T(0);
+          for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int m = 0; m < NM; ++m) u[v][m] = T(0);
-          }
+            for (int m = 1; m < NM; ++m) u[v][m] = T(0);
         }
 
         // ---- horizontal face between rows t-1 and t (once per column) ----
@@ -305,12 +302,10 @@ struct Stage2D {
           for (int g = 0; g < NQ; ++g) {
             T bot[NV];
             trace_at(u, &TH.v[0], g, bot);
-            if (prevRow && rowv) llf2d<EQ, 1>(topPrev[g], bot, Fh[g], gam, gm1, ax, ay);
-            else if (rowv) llf2d<EQ, 1>(bot, bot, Fh[g], gam, gm1, ax, ay);
-            else llf2d<EQ, 1>(topPrev[g], topPrev[g], Fh[g], gam, gm1, ax, ay);
+            llf2d<EQ, 1>(topPrev[g], bot, Fh[g], gam, gm1, ax, ay);
           }
           // finalise u~ of row t-1 with its top-face term
-          if (t - 1 >= yb - 1 && t - 1 <= ye && prevRow) {
+          if (t - 1 >= yb - 1 && t - 1 <= ye) {
             const int s = slot_of(t - 1);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -338,7 +333,7 @@ struct Stage2D {
         }
 
         // ---- partial u~ of row t: bottom face, vertical faces, volume, RK combination ----
-        if (t >= yb - 1 && t <= ye && rowv) {
+        if (t >= yb - 1 && t <= ye) {
           T acc[NV][NM];
           T phiR[NV], phiL[NV], phiB[NV];
 #pragma unroll
@@ -365,14 +360,9 @@ struct Stage2D {
             trace_at(u, &TV.v[NQ * NM], g, tr);
 #pragma unroll
             for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[v], 1);
-            if (rbnd) {
-#pragma unroll
-              for (int v = 0; v < NV; ++v) nb[v] = tr[v];
-            }
             llf2d<EQ, 0>(tr, nb, FR, gam, gm1, ax, ay);
 #pragma unroll
             for (int v = 0; v < NV; ++v) FL[v] = shfl_up_t(FR[v], 1);
-            if (lbnd) llf2d<EQ, 0>(tl, tl, FL, gam, gm1, ax, ay);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
               phiR[v] += (T)GR::w(g) * FR[v];
@@ -420,31 +410,38 @@ struct Stage2D {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if constexpr (PR::MIXED) {
-              // cell average in double-float from the edge integrals, each computed once per edge
+              // cell average in double-float from the edge integrals, each computed once per edge:
+              // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B - Phi_T)
               const df cx = df_from_double(a.c1 * ctl.dt * 0.5 / a.hx);
               const df cy = df_from_double(a.c1 * ctl.dt * 0.5 / a.hy);
-              df m0 = df_mul(df_from_double(a.c1), df{u[v][0], lo0[v]});
+              df m0{u[v][0], lo0[v]};
+              if (a.stage > 0) {
+                const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
+                m0 = df_add(m0, df_mul(df_from_double(a.c0), d));
+              }
               m0 = df_add(m0, df_mul_f(cx, phiL[v]));
               m0 = df_add(m0, df_mul_f(cx, -phiR[v]));
               m0 = df_add(m0, df_mul_f(cy, phiB[v]));
-              if (a.stage > 0) m0 = df_add(m0, df_mul(df_from_double(a.c0), df{un_[v][0], unlo[v]}));
               *slot_ptr(ws, s, v, 0, lane) = m0.hi;
               *slot_ptr(ws, s, v, NM, lane) = m0.lo;
             }
 #pragma unroll
             for (int m = PR::MIXED ? 1 : 0; m < NM; ++m) {
               const T R = (T)(0.5 * (2 * PP[m] + 1) * (2 * QQ[m] + 1)) * acc[v][m];
-              T val = (T)a.c1 * u[v][m] + c1dt * R;
-              if (a.stage > 0) val += (T)a.c0 * un_[v][m];
+              // u + c0 (u^n - u) + c1 dt R  (= c0 u^n + c1 (u + dt R) with c0 + c1 = 1 kept exact)
+              T val = u[v][m] + c1dt * R;
+              if (a.stage > 0) val += (T)a.c0 * (un_[v][m] - u[v][m]);
               *slot_ptr(ws, s, v, m, lane) = val;
             }
           }
         }
 
         // ---- jumps of u~ and the filter of row t-2 ----
-        const bool r1 = (t - 1 >= yb - 1 && t - 1 <= ye) && (pery || (t - 1 >= 0 && t - 1 < ny));
-        const bool r2 = (t - 2 >= yb - 1) && (pery || (t - 2 >= 0 && t - 2 < ny));
-        const bool filt_row = (t - 2 >= yb && t - 2 < ye) && r2;
+        const bool r1 = (t - 1 >= yb - 1 && t - 1 <= ye);
+        const bool r2 = (t - 2 >= yb - 1);
+        const bool g1 = !pery && (t - 1 < 0 || t - 1 >= ny);   // row t-1 is a ghost row
+        const bool g2 = !pery && (t - 2 < 0 || t - 2 >= ny);
+        const bool filt_row = (t - 2 >= yb && t - 2 < ye);
         const bool need_v = t - 1 <= ye - 1;        // row t-1 will be filtered next iteration
         T AVcur[NV][LMAX + 1], SHface[NV][LMAX + 1];
 #pragma unroll
@@ -460,6 +457,27 @@ struct Stage2D {
             for (int m = 0; m < NM; ++m) {
               uv[m] = *slot_ptr(ws, s1, v, m, lane);
               u2[m] = r2 ? *slot_ptr(ws, s2, v, m, lane) : T(0);
+            }
+            // ghost rows and columns: the constant state of the adjacent interior cell's u~ average
+            if (g1) {
+              uv[0] = u2[0];
+#pragma unroll
+              for (int m = 1; m < NM; ++m) uv[m] = T(0);
+            }
+            if (g2) {
+              u2[0] = uv[0];
+#pragma unroll
+              for (int m = 1; m < NM; ++m) u2[m] = T(0);
+            }
+            {
+              const T v_r = shfl_down_t(uv[0], 1), v_l = shfl_up_t(uv[0], 1);
+              const T w_r = shfl_down_t(u2[0], 1), w_l = shfl_up_t(u2[0], 1);
+              if (gcol) {
+                uv[0] = x < 0 ? v_r : v_l;
+                u2[0] = x < 0 ? w_r : w_l;
+#pragma unroll
+                for (int m = 1; m < NM; ++m) uv[m] = u2[m] = T(0);
+              }
             }
             T svr[LMAX + 1], sh[LMAX + 1];
 #pragma unroll
@@ -487,15 +505,10 @@ struct Stage2D {
               if (r2) sh[l] += T(0.5) * (fabs(c00 - t01) + fabs(c10 - t11));
             }
             if (need_v) {
-              if (rbnd) {
-#pragma unroll
-                for (int l = 0; l <= LMAX; ++l) svr[l] = T(0);
-              }
               T run = T(0);
 #pragma unroll
               for (int l = 0; l <= LMAX; ++l) {
-                T svl = shfl_up_t(svr[l], 1);
-                if (lbnd) svl = T(0);
+                const T svl = shfl_up_t(svr[l], 1);
                 run += wx[l] * (svl + svr[l]);
                 AVcur[v][l] = run;
               }
@@ -560,7 +573,6 @@ struct Stage2D {
           }
 #pragma unroll
         for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
-        prevRow = rowv;
       }
     }
     stage_end(a.sc, a.stage, my_rate, my_ok, red);
