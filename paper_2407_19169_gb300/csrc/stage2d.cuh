@@ -118,7 +118,9 @@ struct Stage2D {
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
 
-  static constexpr size_t slot_bytes_per_warp() { return sizeof(T) * 3 * NV * NME * 32; }
+  // per-warp shared memory: 3 row slots of u~ plus the partial damping Q[v][l-1] of one row
+  static constexpr size_t warp_bytes() { return sizeof(T) * (3 * NV * NME + NV * LMAX) * 32; }
+  static constexpr size_t slot_bytes_per_warp() { return warp_bytes(); }
 
   // ---- compile-time tables (evaluated by the front end) ----
   // mode degrees and total degree l = p + q
@@ -228,13 +230,18 @@ struct Stage2D {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
     double* red = (double*)smem;                                  // 32 doubles for stage_end
-    T* ws = (T*)(smem + 256 + slot_bytes_per_warp() * wib);
+    T* ws = (T*)(smem + 256 + warp_bytes() * wib);                // 3 row slots
+    T* wq = ws + 3 * NV * NME * 32;                               // Q[v][l-1] of the next row to filter
     const long long gw = (long long)blockIdx.x * warps_per_block + wib;
     const bool active = gw < (long long)a.nstrips * a.nchunks;
     const int nx = a.nx, ny = a.ny;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax, ay = (T)a.ay;
     const T inv_hx = (T)(1.0 / a.hx), inv_hy = (T)(1.0 / a.hy);
-    const T c1dt = (T)a.c1 * dt;
+    const T c1dt = (T)(a.c1 * ctl.dt), c0 = (T)a.c0;
+    // double-float coefficients of the cell-average update (computed once, off the cell loop)
+    const df dfx = df_from_double(a.c1 * ctl.dt * 0.5 / a.hx);
+    const df dfy = df_from_double(a.c1 * ctl.dt * 0.5 / a.hy);
+    const df dfc0 = df_from_double(a.c0);
     // powers of 2/h for physical derivatives; weights m(m+1) h^m of the m-th derivative jumps
     T px[K + 1], py[K + 1], wx[LMAX + 1], wy[LMAX + 1];
     {
@@ -256,6 +263,7 @@ struct Stage2D {
       }
     }
     double my_rate = 0.0;
+    T my_rate_t = T(0);
     bool my_ok = true;
 
     if (active) {
@@ -271,15 +279,13 @@ struct Stage2D {
       const int ye = min(yb + a.H, ny);
 
       T topPrev[NQ][NV];
-      T AVprev[NV][LMAX + 1], AHbotPrev[NV][LMAX + 1];
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int l = 0; l <= LMAX; ++l) AVprev[v][l] = AHbotPrev[v][l] = T(0);
 #pragma unroll
       for (int g = 0; g < NQ; ++g)
 #pragma unroll
         for (int v = 0; v < NV; ++v) topPrev[g][v] = T(0);
+      // cell-average quantities of the row filtered next (row t-2 at iteration t)
+      T bx2 = T(0), by2 = T(0), invH2 = T(0);
+      bool phys2 = true;
 
 #pragma unroll 1
       for (int t = yb - 2; t <= ye + 1; ++t) {
@@ -314,7 +320,7 @@ struct Stage2D {
 #pragma unroll
                 for (int g = 0; g < NQ; ++g) phi += (T)GR::w(g) * Fh[g][v];
                 df acc0{*slot_ptr(ws, s, v, 0, lane), *slot_ptr(ws, s, v, NM, lane)};
-                acc0 = df_add(acc0, df_mul_f(df_from_double(-a.c1 * ctl.dt * 0.5 / a.hy), phi));
+                acc0 = df_add(acc0, df_mul_f(dfy, -phi));
                 *slot_ptr(ws, s, v, 0, lane) = acc0.hi;
                 *slot_ptr(ws, s, v, NM, lane) = acc0.lo;
               }
@@ -384,13 +390,13 @@ struct Stage2D {
               T uq[NV], fx[NV], fy[NV];
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
-                T s = T(0);
+                T sacc = T(0);
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
                   const double c = VE[base + m];
-                  if (c != 0.0) s += u[v][m] * (T)c;
+                  if (c != 0.0) sacc += u[v][m] * (T)c;
                 }
-                uq[v] = s;
+                uq[v] = sacc;
               }
               flux2d_xy<EQ>(uq, fx, fy, gm1, ax, ay);
 #pragma unroll
@@ -412,16 +418,14 @@ struct Stage2D {
             if constexpr (PR::MIXED) {
               // cell average in double-float from the edge integrals, each computed once per edge:
               // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B - Phi_T)
-              const df cx = df_from_double(a.c1 * ctl.dt * 0.5 / a.hx);
-              const df cy = df_from_double(a.c1 * ctl.dt * 0.5 / a.hy);
               df m0{u[v][0], lo0[v]};
               if (a.stage > 0) {
                 const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
-                m0 = df_add(m0, df_mul(df_from_double(a.c0), d));
+                m0 = df_add(m0, df_mul(dfc0, d));
               }
-              m0 = df_add(m0, df_mul_f(cx, phiL[v]));
-              m0 = df_add(m0, df_mul_f(cx, -phiR[v]));
-              m0 = df_add(m0, df_mul_f(cy, phiB[v]));
+              m0 = df_add(m0, df_mul_f(dfx, phiL[v]));
+              m0 = df_add(m0, df_mul_f(dfx, -phiR[v]));
+              m0 = df_add(m0, df_mul_f(dfy, phiB[v]));
               *slot_ptr(ws, s, v, 0, lane) = m0.hi;
               *slot_ptr(ws, s, v, NM, lane) = m0.lo;
             }
@@ -430,25 +434,33 @@ struct Stage2D {
               const T R = (T)(0.5 * (2 * PP[m] + 1) * (2 * QQ[m] + 1)) * acc[v][m];
               // u + c0 (u^n - u) + c1 dt R  (= c0 u^n + c1 (u + dt R) with c0 + c1 = 1 kept exact)
               T val = u[v][m] + c1dt * R;
-              if (a.stage > 0) val += (T)a.c0 * (un_[v][m] - u[v][m]);
+              if (a.stage > 0) val += c0 * (un_[v][m] - u[v][m]);
               *slot_ptr(ws, s, v, m, lane) = val;
             }
           }
         }
 
-        // ---- jumps of u~ and the filter of row t-2 ----
+        // ---- jumps of u~; the filter of row t-2 ----
+        // Row t-1 is final. Its vertical-face jumps and the jump of the face (t-2 | t-1) give, per
+        // variable v and total degree l, Q_v(l) = beta^x AV_v(l) + beta^y SH_v(l) for row t-1 (kept
+        // in shared memory until its top face is known) and the top-face term of row t-2.
         const bool r1 = (t - 1 >= yb - 1 && t - 1 <= ye);
-        const bool r2 = (t - 2 >= yb - 1);
         const bool g1 = !pery && (t - 1 < 0 || t - 1 >= ny);   // row t-1 is a ghost row
         const bool g2 = !pery && (t - 2 < 0 || t - 2 >= ny);
         const bool filt_row = (t - 2 >= yb && t - 2 < ye);
-        const bool need_v = t - 1 <= ye - 1;        // row t-1 will be filtered next iteration
-        T AVcur[NV][LMAX + 1], SHface[NV][LMAX + 1];
+        const bool need_v = (t - 1 >= yb && t - 1 < ye);      // row t-1 is filtered next iteration
+        T bx1 = T(0), by1 = T(0), invH1 = T(0);
+        bool phys1 = true;
+        if (r1) {
+          T ub[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
+          for (int v = 0; v < NV; ++v) ub[v] = *slot_ptr(ws, slot_of(t - 1), v, 0, lane);
+          avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx1, by1, invH1, phys1);
+        }
+        T sig[LMAX + 1];
 #pragma unroll
-          for (int l = 0; l <= LMAX; ++l) AVcur[v][l] = SHface[v][l] = T(0);
-        if (a.filter_on && r1) {
+        for (int l = 0; l <= LMAX; ++l) sig[l] = T(0);
+        if (a.filter_on && (need_v || filt_row)) {
           const int s1 = slot_of(t - 1), s2 = slot_of(t - 2);
 #pragma unroll 1
           for (int v = 0; v < NV; ++v) {
@@ -456,7 +468,7 @@ struct Stage2D {
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
               uv[m] = *slot_ptr(ws, s1, v, m, lane);
-              u2[m] = r2 ? *slot_ptr(ws, s2, v, m, lane) : T(0);
+              u2[m] = *slot_ptr(ws, s2, v, m, lane);
             }
             // ghost rows and columns: the constant state of the adjacent interior cell's u~ average
             if (g1) {
@@ -502,24 +514,17 @@ struct Stage2D {
                 const T n0 = shfl_down_t(c00, 1), n1 = shfl_down_t(c01, 1);
                 svr[l] += T(0.5) * (fabs(c10 - n0) + fabs(c11 - n1));
               }
-              if (r2) sh[l] += T(0.5) * (fabs(c00 - t01) + fabs(c10 - t11));
+              sh[l] += T(0.5) * (fabs(c00 - t01) + fabs(c10 - t11));
             }
-            if (need_v) {
-              T run = T(0);
+            T av = T(0), shc = T(0);
 #pragma unroll
-              for (int l = 0; l <= LMAX; ++l) {
-                const T svl = shfl_up_t(svr[l], 1);
-                run += wx[l] * (svl + svr[l]);
-                AVcur[v][l] = run;
-              }
-            }
-            if (r2) {
-              T run = T(0);
-#pragma unroll
-              for (int l = 0; l <= LMAX; ++l) {
-                run += wy[l] * sh[l];
-                SHface[v][l] = run;
-              }
+            for (int l = 0; l <= LMAX; ++l) {
+              shc += wy[l] * sh[l];
+              if (need_v) av += wx[l] * (shfl_up_t(svr[l], 1) + svr[l]);
+              if (l == 0) continue;
+              T* q = wq + ((v * LMAX + (l - 1)) << 5) + lane;
+              if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * shc);   // Q of row t-2 + its top face
+              if (need_v) *q = bx1 * av + by1 * shc;                      // Q of row t-1 (bottom face)
             }
           }
         }
@@ -527,30 +532,18 @@ struct Stage2D {
           const int s2 = slot_of(t - 2);
           const int ty2 = pery ? ((t - 2) % ny + ny) % ny : t - 2;
           const long long cell2 = (long long)ty2 * nx + xc;
-          T uo[NV][NM], lo[NV], ub[NV];
+          T uo[NV][NM], lo[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
 #pragma unroll
             for (int m = 0; m < NM; ++m) uo[v][m] = *slot_ptr(ws, s2, v, m, lane);
             if constexpr (PR::MIXED) lo[v] = *slot_ptr(ws, s2, v, NM, lane);
             else lo[v] = T(0);
-            ub[v] = uo[v][0];
           }
-          T bx, by, invH;
-          bool phys;
-          avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx, by, invH, phys);
           if (a.filter_on) {
             T fac[LMAX + 1];
 #pragma unroll
-            for (int l = 1; l <= LMAX; ++l) {
-              T best = T(0);
-#pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                const T sgm = bx * AVprev[v][l] + by * (AHbotPrev[v][l] + SHface[v][l]);
-                best = (sgm > best || sgm != sgm) ? sgm : best;
-              }
-              fac[l] = exp(-(best * invH) * dt);
-            }
+            for (int l = 1; l <= LMAX; ++l) fac[l] = exp(-(sig[l] * invH2) * dt);
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -558,23 +551,26 @@ struct Stage2D {
           }
           if (out_lane) {
             ST::store(a.uout, a.ncell, cell2, uo, lo);
-            if (!phys) my_ok = false;
-            const double r = (double)bx / a.hx + (double)by / a.hy;
-            my_rate = (r > my_rate || r != r) ? r : my_rate;
+            if (!phys2) my_ok = false;
+            if constexpr (PR::MIXED) {
+              const T r = bx2 * inv_hx + by2 * inv_hy;
+              my_rate_t = nan_max(r, my_rate_t);
+            } else {
+              const double r = (double)bx2 / a.hx + (double)by2 / a.hy;
+              my_rate = (r > my_rate || r != r) ? r : my_rate;
+            }
           }
         }
         // carry to the next row
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-          for (int l = 0; l <= LMAX; ++l) {
-            AVprev[v][l] = AVcur[v][l];
-            AHbotPrev[v][l] = SHface[v][l];
-          }
+        bx2 = bx1;
+        by2 = by1;
+        invH2 = invH1;
+        phys2 = phys1;
 #pragma unroll
         for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
       }
     }
+    if constexpr (PR::MIXED) my_rate = (double)my_rate_t;
     stage_end(a.sc, a.stage, my_rate, my_ok, red);
   }
 };
