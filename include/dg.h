@@ -165,6 +165,27 @@ DG_API dg_status dg_dims(const dg_solver* s, int* nvars, int* nmodes, long long*
 /* Number of kernels this solver has launched (stage kernels, projections, reductions, copies). */
 DG_API dg_status dg_kernel_launches(const dg_solver* s, long long* launches);
 
+/* One FP64 SSP-RK3 step (jump filter after each stage) from u_in to u_out that allocates no device
+ * memory. The paper has no counterpart to this entry point; it is for callers that cannot call
+ * cudaMalloc where they want a step: code running while a stream is being captured into a CUDA graph,
+ * frameworks that own every byte of device memory through a pre-planned arena, and latency-critical
+ * loops that must not allocate or synchronise. They pass the input and output states; the two
+ * intermediate stage states and the step-control scalars live in one static device array of
+ * 32 MiB + 256 B, which every GPU that loads this library holds until the process exits. Meshes whose
+ * two FP64 stage states do not fit in 32 MiB are rejected with DG_ERR_BUDGET before anything runs.
+ *   mesh, degree, equation, params: as for dg_create; params->precision must be DG_PREC_FP64.
+ *   u_in, u_out: device pointers to canonical FP64 states (dg_state_size doubles); must not overlap.
+ *   dt_taken: host pointer or NULL. If non-NULL the call synchronises the stream, stores the step size
+ *     and returns DG_ERR_NONPHYSICAL if a cell average became non-physical; if NULL nothing is read
+ *     back and the call returns as soon as the kernels are enqueued.
+ *   cuda_stream: the stream the kernels run on (NULL = the legacy default stream).
+ * The first call on a device (with that device current) looks up the array's device address once;
+ * make that first call before any stream capture. All calls share the array, which keeps the last
+ * call's contents (each call resets the scalars it uses): calls that overlap on the GPU race. */
+DG_API dg_status dg_step_noalloc(const dg_mesh* mesh, int degree, int equation,
+                                 const dg_filter_params* params, const double* u_in, double* u_out,
+                                 double* dt_taken, void* cuda_stream);
+
 /* Release all device memory the library allocated for this solver. NULL is accepted. */
 DG_API dg_status dg_destroy(dg_solver* s);
 

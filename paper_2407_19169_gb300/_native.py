@@ -26,7 +26,7 @@ IC_SINE, IC_RIEMANN1D, IC_ENTROPY1D, IC_QUADRANT2D, IC_VORTEX2D = range(5)
 EXPORTED = ["dg_status_string", "dg_last_error", "dg_params_default", "dg_workspace_size", "dg_create",
             "dg_set_initial", "dg_state_size", "dg_write_state", "dg_write_state_device", "dg_read_state",
             "dg_read_state_device", "dg_step", "dg_advance_to", "dg_advance_steps", "dg_sync", "dg_mass",
-            "dg_dims", "dg_kernel_launches", "dg_destroy"]
+            "dg_dims", "dg_kernel_launches", "dg_destroy", "dg_step_noalloc"]
 
 
 class Mesh(C.Structure):
@@ -83,6 +83,7 @@ def load():
         "dg_dims": (I, [V, P(I), P(I), P(LL)]),
         "dg_kernel_launches": (I, [V, P(LL)]),
         "dg_destroy": (I, [V]),
+        "dg_step_noalloc": (I, [P(Mesh), I, I, P(Params), V, V, dp, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
