@@ -88,7 +88,9 @@ typedef struct {
  *             double-float with compensated error-free updates)
  *   workspace optional caller-owned device buffer of at least dg_workspace_size bytes, aligned to
  *             256 bytes; NULL = the library allocates
- *   tile_rows rows per warp in the 2D stage kernel, 0 = default */
+ *   tile_rows rows per warp in the 2D stage kernel, 0 = default
+ *   tile_warps warps per thread block of the 2D stage kernel, 0 = default (both are tile-shape knobs
+ *             for the autotuner; results do not depend on them) */
 typedef struct {
   int enabled;
   double cfl;
@@ -100,6 +102,7 @@ typedef struct {
   void* workspace;
   size_t workspace_bytes;
   int tile_rows;
+  int tile_warps;
 } dg_filter_params;
 
 typedef struct dg_solver dg_solver; /* opaque, library-owned */
@@ -152,6 +155,20 @@ DG_API dg_status dg_advance_to(dg_solver* s, double T, long long max_steps, long
 /* Enqueue nsteps unclipped steps on the solver's stream without synchronising (for timing and for
  * overlapping several solvers). Use dg_sync to wait and collect the status. */
 DG_API dg_status dg_advance_steps(dg_solver* s, long long nsteps);
+
+/* Set the device stop condition: stepping stops (further steps are no-ops) once t reaches T_end
+ * (the last step is clipped to land on it) or after max_steps more steps. Synchronises. */
+DG_API dg_status dg_set_target(dg_solver* s, double T_end, long long max_steps);
+
+/* Batched stepping (many uneven solves at once): advance every solver in solvers[0..n-1] by up to
+ * `steps` SSP-RK3 steps. Solvers of the same (dimension, degree) class share one work-list kernel
+ * per stage whose warps take tile items from all instances of the class; the classes run as
+ * parallel branches of one CUDA graph that holds a whole step and is replayed `steps` times on the
+ * first solver's stream. Each solver keeps its own dt (its own CFL max) and stop condition
+ * (dg_set_target): a solver that reaches its T_end or step limit idles. Results equal those of the
+ * same solver stepped alone. Supported: Euler, FP32 form, 1D or 2D Q^k; all on one device.
+ * Synchronises; returns DG_ERR_NONPHYSICAL if any solver failed (check each with dg_sync). */
+DG_API dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps);
 
 /* Wait for the solver's stream; report the time, the completed step count and any error. */
 DG_API dg_status dg_sync(dg_solver* s, double* t, long long* steps);

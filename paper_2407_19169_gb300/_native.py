@@ -26,7 +26,8 @@ IC_SINE, IC_RIEMANN1D, IC_ENTROPY1D, IC_QUADRANT2D, IC_VORTEX2D = range(5)
 EXPORTED = ["dg_status_string", "dg_last_error", "dg_params_default", "dg_workspace_size", "dg_create",
             "dg_set_initial", "dg_state_size", "dg_write_state", "dg_write_state_device", "dg_read_state",
             "dg_read_state_device", "dg_step", "dg_advance_to", "dg_advance_steps", "dg_sync", "dg_mass",
-            "dg_dims", "dg_kernel_launches", "dg_destroy", "dg_step_noalloc"]
+            "dg_dims", "dg_kernel_launches", "dg_destroy", "dg_step_noalloc", "dg_set_target",
+            "dg_batch_run"]
 
 
 class Mesh(C.Structure):
@@ -37,7 +38,8 @@ class Mesh(C.Structure):
 class Params(C.Structure):
     _fields_ = [("enabled", C.c_int), ("cfl", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double * 2), ("basis", C.c_int), ("nq", C.c_int), ("precision", C.c_int),
-                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("tile_rows", C.c_int)]
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("tile_rows", C.c_int),
+                ("tile_warps", C.c_int)]
 
 
 class DGError(RuntimeError):
@@ -84,6 +86,8 @@ def load():
         "dg_kernel_launches": (I, [V, P(LL)]),
         "dg_destroy": (I, [V]),
         "dg_step_noalloc": (I, [P(Mesh), I, I, P(Params), V, V, dp, V]),
+        "dg_set_target": (I, [V, D, LL]),
+        "dg_batch_run": (I, [P(V), I, LL]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -105,12 +109,18 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def batch_run(solvers, steps: int) -> int:
+    """dg_batch_run over a list of Solver objects; returns the status (0 = all ok)."""
+    arr = (C.c_void_p * len(solvers))(*[s.handle.value for s in solvers])
+    return load().dg_batch_run(arr, len(solvers), steps)
+
+
 class Solver:
     """One DG solve on the current CUDA device (a handle from dg_create)."""
 
     def __init__(self, dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(BC_PERIODIC,) * 4, k=2,
                  eq=EQ_BURGERS, filter=1, cfl=0.1, gamma=1.4, adv=(1.0, 0.0), basis=BASIS_Q,
-                 precision=PREC_FP64, stream=None, tile_rows=0, workspace=None):
+                 precision=PREC_FP64, stream=None, tile_rows=0, workspace=None, tile_warps=0):
         L = load()
         self.mesh = Mesh(dim, nx, ny, x0, x1, y0, y1, (C.c_int * 4)(*bc))
         self.params = Params()
@@ -122,6 +132,7 @@ class Solver:
         self.params.basis = basis
         self.params.precision = precision
         self.params.tile_rows = tile_rows
+        self.params.tile_warps = tile_warps
         self._workspace = workspace  # keep a caller tensor alive
         if workspace is not None:
             self.params.workspace = workspace.data_ptr()
@@ -198,6 +209,9 @@ class Solver:
 
     def advance_steps(self, n: int) -> None:
         check(load().dg_advance_steps(self.handle, n), "dg_advance_steps")
+
+    def set_target(self, T_end: float, max_steps: int = 1 << 62) -> None:
+        check(load().dg_set_target(self.handle, T_end, max_steps), "dg_set_target")
 
     def sync(self):
         t = C.c_double()

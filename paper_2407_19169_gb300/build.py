@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
-UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "dg_noalloc.cu"]
+UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "dg_noalloc.cu", "dg_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]

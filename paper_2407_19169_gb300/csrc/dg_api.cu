@@ -15,6 +15,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "solver.h"
 #include "stage1d.cuh"
 
 using namespace dgk;
@@ -31,32 +32,7 @@ static dg_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-struct dg_solver {
-  dg_mesh mesh;
-  int k, eq, dim, basis, prec, filter_on, H, warps_per_block;
-  double cfl, gamma, ax, ay;
-  AuxGeom geom;
-  size_t ndof, sbytes;
-  cudaStream_t stream;
-  bool own_stream;
-  bool own_mem;
-  void* mem;
-  size_t mem_bytes;
-  void* buf[3];
-  double* canon;        // FP64 conversion scratch (FP32 form only)
-  double* partials;     // mass partial sums
-  double* dmass;        // mass result
-  DevScalars* sc;
-  DevScalars* h_sc;     // pinned mirror
-  long long h_step;     // host's record of the device step count (buffer parity)
-  StageLauncher L;
-  unsigned grid, block;
-  size_t smem;
-  int nstrips, nchunks, nwarps1d;
-  cudaGraphExec_t pair_exec;
-  bool pair_ready;
-  long long launches;
-};
+
 
 extern "C" const char* dg_status_string(int s) {
   switch (s) {
@@ -181,7 +157,7 @@ extern "C" dg_status dg_workspace_size(const dg_mesh* mesh, int degree, int equa
   return DG_OK;
 }
 
-static dg_status setup_launch(dg_solver* s, int tile_rows) {
+static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (s->dim == 1) {
     s->L = stage1d_launcher(s->k, s->eq, s->prec);
     if (!s->L.launch) return DG_ERR_UNSUPPORTED;
@@ -211,6 +187,7 @@ static dg_status setup_launch(dg_solver* s, int tile_rows) {
   size_t per_warp = s->L.slot_bytes_per_warp;
   int wpb = (int)((200 * 1024 - 256) / per_warp);
   if (wpb > 8) wpb = 8;
+  if (tile_warps > 0 && tile_warps < wpb) wpb = tile_warps;
   if (wpb < 1) return DG_ERR_UNSUPPORTED;
   s->warps_per_block = wpb;
   s->block = 32 * wpb;
@@ -268,7 +245,7 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
   s->ndof = (size_t)s->geom.nv * s->geom.nm * s->geom.ncell;
   s->sbytes = state_bytes(s->geom);
 
-  st = setup_launch(s, params->tile_rows);
+  st = setup_launch(s, params->tile_rows, params->tile_warps);
   if (st != DG_OK) { dg_destroy(s); return st; }
 
   Layout Lo = layout_of(s->geom);
@@ -423,6 +400,10 @@ static dg_status pull_control(dg_solver* s) {
   s->h_step = s->h_sc->step;
   return DG_OK;
 }
+
+namespace dgk {
+dg_status solver_pull_control(dg_solver* s) { return pull_control(s); }
+}  // namespace dgk
 
 static const void* current_state(const dg_solver* s) { return s->buf[s->h_step & 1]; }
 
@@ -585,6 +566,11 @@ extern "C" dg_status dg_step(dg_solver* s, double* dt_taken) {
   if (s->h_sc->err) return DG_ERR_NONPHYSICAL;
   if (dt_taken) *dt_taken = s->h_sc->dt;
   return DG_OK;
+}
+
+extern "C" dg_status dg_set_target(dg_solver* s, double T_end, long long max_steps) {
+  if (!s || max_steps < 0 || !(T_end == T_end)) return DG_ERR_ARG;
+  return set_target(s, T_end, max_steps);
 }
 
 extern "C" dg_status dg_advance_steps(dg_solver* s, long long nsteps) {

@@ -1,0 +1,354 @@
+// dg_batch.cu — batched stepping of many uneven solves (dg_batch_run).
+//
+// Work decomposition: every solver is an instance; the tile items of an instance are its warp
+// strips (1D) or (strip, row-chunk) tiles (2D), exactly the items its own stage kernel would run.
+// Instances of one (dimension, degree) class share one grid-stride work-list kernel per stage: a
+// warp takes the next item of the class, finds its instance by binary search over the instances'
+// first-item offsets, and runs the same item() body as the single-solve kernel with that instance's
+// dt and buffers. Large and small instances therefore share the GPU in proportion to their work.
+//
+// Step control per instance, without inter-block waits: a begin kernel computes each instance's
+// dt from its CFL rate max (clipped to its T_end), the three stage launches follow, and an end
+// kernel advances t and the step count. A whole step — begin, the classes' stage kernels as
+// parallel graph branches, end — is captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "solver.h"
+#include "stage1d.cuh"
+
+namespace dgk {
+
+struct BatchInst {
+  void* buf[3];
+  DevScalars* sc;
+  long long ncell;
+  long long item0;     // first work item of this instance within its class
+  int nx, ny, bcx, bcy, H, nstrips, nchunks, filter_on;
+  double hx, hy, gamma, ax, ay, cfl;
+};
+
+struct BatchArgs {
+  const BatchInst* inst;   // the class's instances, item0 ascending
+  int ninst;
+  long long nitems;
+  int stage;
+};
+
+__device__ __forceinline__ int find_inst(const BatchInst* inst, int n, long long w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].item0 <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Fold one item's rate max and physicality into its instance (lane 0 of the warp).
+__device__ __forceinline__ void item_end(const BatchInst& I, int stage, long long step, double r, bool ok) {
+  r = warp_max(r);
+  const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&I.sc->err, ERRB_NONPHYS);
+    if (stage == 2) atomic_max_nonneg(&I.sc->rate_bits[(step + 1) & 1], r);
+  }
+  __syncwarp();
+}
+
+template <int K, int EQ, int B, class PR>
+__global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
+  using S = Stage2D<K, EQ, B, PR>;
+  using T = typename PR::T;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int wib = threadIdx.x >> 5;
+  T* ws = (T*)(dyn_smem + S::warp_bytes() * wib);
+  const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + wib; w < b.nitems; w += nwt) {
+    const BatchInst& I = b.inst[find_inst(b.inst, b.ninst, w)];
+    volatile DevScalars* vs = I.sc;
+    if (vs->done | vs->err) continue;
+    const long long step = vs->step;
+    const double dt = vs->dt;
+    const int p = (int)(step & 1);
+    Stage2DArgs a;
+    a.uin = b.stage == 0 ? I.buf[p] : (b.stage == 1 ? I.buf[1 - p] : I.buf[2]);
+    a.un = I.buf[p];
+    a.uout = b.stage == 1 ? I.buf[2] : I.buf[1 - p];
+    a.nx = I.nx;
+    a.ny = I.ny;
+    a.ncell = I.ncell;
+    a.hx = I.hx;
+    a.hy = I.hy;
+    a.bcx = I.bcx;
+    a.bcy = I.bcy;
+    a.c0 = b.stage == 0 ? 0.0 : (b.stage == 1 ? 0.75 : 1.0 / 3.0);
+    a.c1 = b.stage == 0 ? 1.0 : (b.stage == 1 ? 0.25 : 2.0 / 3.0);
+    a.stage = b.stage;
+    a.filter_on = I.filter_on;
+    a.gamma = I.gamma;
+    a.ax = I.ax;
+    a.ay = I.ay;
+    a.cfl = I.cfl;
+    a.H = I.H;
+    a.nstrips = I.nstrips;
+    a.nchunks = I.nchunks;
+    a.sc = I.sc;
+    const long long local = w - I.item0;
+    double r = 0.0;
+    T rt = T(0);
+    bool ok = true;
+    S::item(a, dt, (int)(local % I.nstrips), (int)(local / I.nstrips), ws, r, rt, ok);
+    if constexpr (PR::MIXED) r = (double)rt;
+    item_end(I, b.stage, step, r, ok);
+  }
+}
+
+template <int K, int EQ, class PR>
+__global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
+  using S = Stage1D<K, EQ, PR>;
+  using T = typename PR::T;
+  const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < b.nitems; w += nwt) {
+    const BatchInst& I = b.inst[find_inst(b.inst, b.ninst, w)];
+    volatile DevScalars* vs = I.sc;
+    if (vs->done | vs->err) continue;
+    const long long step = vs->step;
+    const double dt = vs->dt;
+    const int p = (int)(step & 1);
+    Stage1DArgs a;
+    a.uin = b.stage == 0 ? I.buf[p] : (b.stage == 1 ? I.buf[1 - p] : I.buf[2]);
+    a.un = I.buf[p];
+    a.uout = b.stage == 1 ? I.buf[2] : I.buf[1 - p];
+    a.nx = I.nx;
+    a.ncell = I.ncell;
+    a.h = I.hx;
+    a.bc = I.bcx;
+    a.c0 = b.stage == 0 ? 0.0 : (b.stage == 1 ? 0.75 : 1.0 / 3.0);
+    a.c1 = b.stage == 0 ? 1.0 : (b.stage == 1 ? 0.25 : 2.0 / 3.0);
+    a.stage = b.stage;
+    a.filter_on = I.filter_on;
+    a.gamma = I.gamma;
+    a.ax = I.ax;
+    a.cfl = I.cfl;
+    a.nwarps = I.nstrips;
+    a.sc = I.sc;
+    double r = 0.0;
+    T rt = T(0);
+    bool ok = true;
+    S::item(a, dt, w - I.item0, r, rt, ok);
+    if constexpr (PR::MIXED) r = (double)rt;
+    item_end(I, b.stage, step, r, ok);
+  }
+}
+
+// Per-instance dt at the start of a step (the same rule as the single-solve stage 0).
+__global__ void batch_begin_kernel(const BatchInst* inst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  DevScalars* sc = inst[i].sc;
+  if (sc->done | sc->err) return;
+  const long long step = sc->step;
+  const double rate = __longlong_as_double((long long)sc->rate_bits[step & 1]);
+  if (!(rate > 0.0) || !isfinite(rate)) {
+    sc->err |= ERRB_RATE;
+    return;
+  }
+  const double t = sc->t, T = sc->T_end, dtc = inst[i].cfl / rate;
+  const bool last = (t + dtc >= T);
+  sc->dt = last ? T - t : dtc;
+  sc->is_last = last ? 1u : 0u;
+  sc->rate_bits[(step + 1) & 1] = 0ull;
+}
+
+// Per-instance step advance at the end of a step (the single-solve last-block rule).
+__global__ void batch_end_kernel(const BatchInst* inst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  DevScalars* sc = inst[i].sc;
+  if (sc->done | sc->err) return;
+  const double tn = sc->is_last ? sc->T_end : sc->t + sc->dt;
+  const long long st = sc->step + 1;
+  sc->t = tn;
+  sc->step = st;
+  sc->done = (tn >= sc->T_end || st >= sc->max_step) ? 1u : 0u;
+}
+
+struct BatchLauncher {
+  cudaError_t (*launch)(const BatchArgs&, unsigned grid, unsigned block, size_t smem, cudaStream_t s);
+  cudaError_t (*set_smem)(size_t bytes);
+  size_t warp_bytes;
+};
+
+template <int K>
+static cudaError_t launch_b2(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
+  batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M><<<g, bl, sm, s>>>(b);
+  return cudaGetLastError();
+}
+template <int K>
+static cudaError_t smem_b2(size_t bytes) {
+  return cudaFuncSetAttribute(batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+template <int K>
+static cudaError_t launch_b1(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
+  batch1d_kernel<K, EQ_EULER, PrecF32M><<<g, bl, sm, s>>>(b);
+  return cudaGetLastError();
+}
+static cudaError_t smem_none(size_t) { return cudaSuccess; }
+
+static BatchLauncher batch_launcher(int dim, int K) {
+  if (dim == 2) {
+    switch (K) {
+      case 1: return {&launch_b2<1>, &smem_b2<1>, Stage2D<1, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes()};
+      case 2: return {&launch_b2<2>, &smem_b2<2>, Stage2D<2, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes()};
+      case 3: return {&launch_b2<3>, &smem_b2<3>, Stage2D<3, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes()};
+    }
+  } else {
+    switch (K) {
+      case 1: return {&launch_b1<1>, &smem_none, 0};
+      case 2: return {&launch_b1<2>, &smem_none, 0};
+      case 3: return {&launch_b1<3>, &smem_none, 0};
+    }
+  }
+  return {nullptr, nullptr, 0};
+}
+
+}  // namespace dgk
+
+using namespace dgk;
+
+extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps) {
+  if (!solvers || n < 1 || steps < 0) return DG_ERR_ARG;
+  int dev0 = -1;
+  for (int i = 0; i < n; ++i) {
+    const dg_solver* s = solvers[i];
+    if (!s) return DG_ERR_ARG;
+    if (s->eq != DG_EQ_EULER || s->prec != PREC_F32M || (s->dim == 2 && s->basis != DG_BASIS_Q))
+      return DG_ERR_UNSUPPORTED;
+  }
+  if (cudaGetDevice(&dev0) != cudaSuccess) return DG_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if (solver_pull_control(solvers[i]) != DG_OK) return DG_ERR_CUDA;   // also orders prior work
+  if (steps == 0) return DG_OK;
+
+  // classes: (dim, K) -> index dim_index * 3 + K - 1
+  constexpr int NCLS = 6;
+  std::vector<BatchInst> host;
+  host.reserve(n);
+  int cls_begin[NCLS], cls_count[NCLS], cls_wpb[NCLS];
+  long long cls_items[NCLS];
+  for (int c = 0; c < NCLS; ++c) {
+    cls_begin[c] = (int)host.size();
+    cls_items[c] = 0;
+    cls_wpb[c] = 8;
+    const int dim = c < 3 ? 1 : 2, K = c % 3 + 1;
+    for (int i = 0; i < n; ++i) {
+      const dg_solver* s = solvers[i];
+      if (s->dim != dim || s->k != K) continue;
+      BatchInst I;
+      memset(&I, 0, sizeof(I));
+      for (int b = 0; b < 3; ++b) I.buf[b] = s->buf[b];
+      I.sc = s->sc;
+      I.ncell = s->geom.ncell;
+      I.item0 = cls_items[c];
+      I.nx = s->mesh.nx;
+      I.ny = s->dim == 2 ? s->mesh.ny : 1;
+      I.bcx = s->mesh.bc[0];
+      I.bcy = s->dim == 2 ? s->mesh.bc[2] : 0;
+      I.H = s->dim == 2 ? s->H : 1;
+      I.nstrips = s->dim == 2 ? s->nstrips : s->nwarps1d;
+      I.nchunks = s->dim == 2 ? s->nchunks : 1;
+      I.filter_on = s->filter_on;
+      I.hx = s->geom.hx;
+      I.hy = s->geom.hy;
+      I.gamma = s->gamma;
+      I.ax = s->ax;
+      I.ay = s->ay;
+      I.cfl = s->cfl;
+      cls_items[c] += (long long)I.nstrips * I.nchunks;
+      if (s->dim == 2 && s->warps_per_block < cls_wpb[c]) cls_wpb[c] = s->warps_per_block;
+      host.push_back(I);
+    }
+    cls_count[c] = (int)host.size() - cls_begin[c];
+    if (c < 3) cls_wpb[c] = 4;
+  }
+
+  dg_status status = DG_OK;
+  cudaStream_t main = solvers[0]->stream;
+  BatchInst* dinst = nullptr;
+  cudaStream_t side[NCLS] = {};
+  cudaEvent_t fork = nullptr, join[NCLS] = {};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaMalloc(&dinst, sizeof(BatchInst) * host.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dinst, host.data(), sizeof(BatchInst) * host.size(), cudaMemcpyHostToDevice, main);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int c = 0; c < NCLS && e == cudaSuccess; ++c) {
+    e = cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[c], cudaEventDisableTiming);
+  }
+  BatchLauncher BL[NCLS];
+  for (int c = 0; c < NCLS && e == cudaSuccess; ++c) {
+    BL[c] = batch_launcher(c < 3 ? 1 : 2, c % 3 + 1);
+    if (cls_count[c] > 0 && BL[c].set_smem) e = BL[c].set_smem(BL[c].warp_bytes * cls_wpb[c]);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t ce = cudaSuccess;
+    const unsigned nb = (unsigned)((host.size() + 127) / 128);
+    batch_begin_kernel<<<nb, 128, 0, main>>>(dinst, (int)host.size());
+    ce = cudaGetLastError();
+    for (int stage = 0; stage < 3 && ce == cudaSuccess; ++stage) {
+      ce = cudaEventRecord(fork, main);
+      for (int c = 0; c < NCLS && ce == cudaSuccess; ++c) {
+        if (cls_count[c] == 0) continue;
+        BatchArgs b;
+        b.inst = dinst + cls_begin[c];
+        b.ninst = cls_count[c];
+        b.nitems = cls_items[c];
+        b.stage = stage;
+        const int wpb = cls_wpb[c];
+        long long blocks = (cls_items[c] + wpb - 1) / wpb;
+        if (blocks > 152LL * 4) blocks = 152LL * 4;
+        ce = cudaStreamWaitEvent(side[c], fork, 0);
+        if (ce == cudaSuccess)
+          ce = BL[c].launch(b, (unsigned)blocks, 32u * wpb, BL[c].warp_bytes * wpb, side[c]);
+        if (ce == cudaSuccess) ce = cudaEventRecord(join[c], side[c]);
+      }
+      for (int c = 0; c < NCLS && ce == cudaSuccess; ++c)
+        if (cls_count[c] > 0) ce = cudaStreamWaitEvent(main, join[c], 0);
+    }
+    if (ce == cudaSuccess) {
+      batch_end_kernel<<<nb, 128, 0, main>>>(dinst, (int)host.size());
+      ce = cudaGetLastError();
+    }
+    e = cudaStreamEndCapture(main, &graph);
+    if (ce != cudaSuccess) e = ce;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  for (long long i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, main);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+  if (e != cudaSuccess) status = DG_ERR_CUDA;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int c = 0; c < NCLS; ++c) {
+    if (side[c]) cudaStreamDestroy(side[c]);
+    if (join[c]) cudaEventDestroy(join[c]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (dinst) cudaFree(dinst);
+  if (status != DG_OK) return status;
+  int present = 0;
+  for (int c = 0; c < NCLS; ++c) present += cls_count[c] > 0;
+  solvers[0]->launches += steps * (2 + 3LL * present);    // the graph's kernel nodes, once per step
+  for (int i = 0; i < n; ++i) {
+    dg_solver* s = solvers[i];
+    if (solver_pull_control(s) != DG_OK) return DG_ERR_CUDA;
+    if (s->h_sc->err) status = DG_ERR_NONPHYSICAL;
+  }
+  return status;
+}

@@ -46,21 +46,20 @@ struct Stage1D {
   static __device__ __forceinline__ T sd(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ T su(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
 
-  static __device__ void run(const Stage1DArgs& a, unsigned char* smem) {
-    const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
-    if (!ctl.run) return;
-    const T dt = (T)ctl.dt;
+  // One tile item: the 32-cell strip `strip` (28 output cells) of one instance, step size dtd. The
+  // output cells' max CFL rate and physicality are folded into my_rate / my_rate_t and my_ok.
+  static __device__ void item(const Stage1DArgs& a, double dtd, long long strip, double& my_rate,
+                              T& my_rate_t, bool& my_ok) {
+    const T dt = (T)dtd;
     const int lane = threadIdx.x & 31;
-    double* red = (double*)smem;
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const bool active = gw < a.nwarps;
     const int nx = a.nx;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax;
     const T inv_h = (T)(1.0 / a.h), scl = (T)(2.0 / a.h);
-    double my_rate = 0.0;
-    bool my_ok = true;
-    if (active) {
-      const int x = (int)gw * STRIP_OUT - 2 + lane;
+    // double-float coefficients of the cell-average update (once per item, off the cell path)
+    const df dcf = df_from_double(a.c1 * dtd / a.h);
+    const df dc0 = df_from_double(a.c0);
+    {
+      const int x = (int)strip * STRIP_OUT - 2 + lane;
       const bool per = a.bc == BC_PERIODIC;
       const int xc = per ? ((x % nx) + nx) % nx : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
       // outflow: a lane left or right of the mesh is a ghost cell holding the constant state equal
@@ -135,14 +134,13 @@ struct Stage1D {
         ulo[v] = T(0);
         if constexpr (PR::MIXED) {
           // cell average in double-float: u0 + c0 (un0 - u0) + c1 dt/h (F_L - F_R)
-          const df cf = df_from_double(a.c1 * ctl.dt / a.h);
           df m0{u[v][0], lo0[v]};
           if (a.stage > 0) {
             const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
-            m0 = df_add(m0, df_mul(df_from_double(a.c0), d));
+            m0 = df_add(m0, df_mul(dc0, d));
           }
-          m0 = df_add(m0, df_mul_f(cf, FL[v]));
-          m0 = df_add(m0, df_mul_f(cf, -FR[v]));
+          m0 = df_add(m0, df_mul_f(dcf, FL[v]));
+          m0 = df_add(m0, df_mul_f(dcf, -FR[v]));
           ut[v][0] = m0.hi;
           ulo[v] = m0.lo;
         }
@@ -217,10 +215,27 @@ struct Stage1D {
       if (out_lane) {
         ST::store(a.uout, a.ncell, xc, ut, ulo);
         if (!phys) my_ok = false;
-        const double r = (double)bx / a.h;
-        my_rate = (r > my_rate || r != r) ? r : my_rate;
+        if constexpr (PR::MIXED) {
+          my_rate_t = nan_max(bx * inv_h, my_rate_t);
+        } else {
+          const double r = (double)bx / a.h;
+          my_rate = (r > my_rate || r != r) ? r : my_rate;
+        }
       }
     }
+  }
+
+  // Single-instance stage: one warp per strip, step control on the instance's DevScalars.
+  static __device__ void run(const Stage1DArgs& a, unsigned char* smem) {
+    const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
+    if (!ctl.run) return;
+    double* red = (double*)smem;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    double my_rate = 0.0;
+    T my_rate_t = T(0);
+    bool my_ok = true;
+    if (gw < a.nwarps) item(a, ctl.dt, gw, my_rate, my_rate_t, my_ok);
+    if constexpr (PR::MIXED) my_rate = (double)my_rate_t;
     stage_end(a.sc, a.stage, my_rate, my_ok, red);
   }
 };

@@ -210,7 +210,11 @@ struct Stage2D {
     }
   }
 
-  static __device__ void run(const Stage2DArgs& a, unsigned char* smem) {
+  // One tile item: strip `strip` (28 output columns) and row chunk `chunk` of one instance, with step
+  // size dtd. ws: this warp's row slots and Q area in shared memory. The output cells' max CFL rate
+  // and physicality are folded into my_rate (FP64 form) / my_rate_t (FP32 form) and my_ok.
+  static __device__ void item(const Stage2DArgs& a, double dtd, int strip, int chunk, T* ws,
+                              double& my_rate, T& my_rate_t, bool& my_ok) {
     constexpr carr<int, NM> PP = tab_p();
     constexpr carr<int, NM> QQ = tab_q();
     constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
@@ -224,23 +228,16 @@ struct Stage2D {
     constexpr carr<int, NA> A1 = tab_a(0);
     constexpr carr<int, NA> A2 = tab_a(1);
 
-    const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
-    if (!ctl.run) return;
-    const T dt = (T)ctl.dt;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warps_per_block = blockDim.x >> 5;
-    double* red = (double*)smem;                                  // 32 doubles for stage_end
-    T* ws = (T*)(smem + 256 + warp_bytes() * wib);                // 3 row slots
+    const T dt = (T)dtd;
+    const int lane = threadIdx.x & 31;
     T* wq = ws + 3 * NV * NME * 32;                               // Q[v][l-1] of the next row to filter
-    const long long gw = (long long)blockIdx.x * warps_per_block + wib;
-    const bool active = gw < (long long)a.nstrips * a.nchunks;
     const int nx = a.nx, ny = a.ny;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax, ay = (T)a.ay;
     const T inv_hx = (T)(1.0 / a.hx), inv_hy = (T)(1.0 / a.hy);
-    const T c1dt = (T)(a.c1 * ctl.dt), c0 = (T)a.c0;
+    const T c1dt = (T)(a.c1 * dtd), c0 = (T)a.c0;
     // double-float coefficients of the cell-average update (computed once, off the cell loop)
-    const df dfx = df_from_double(a.c1 * ctl.dt * 0.5 / a.hx);
-    const df dfy = df_from_double(a.c1 * ctl.dt * 0.5 / a.hy);
+    const df dfx = df_from_double(a.c1 * dtd * 0.5 / a.hx);
+    const df dfy = df_from_double(a.c1 * dtd * 0.5 / a.hy);
     const df dfc0 = df_from_double(a.c0);
     // powers of 2/h for physical derivatives; weights m(m+1) h^m of the m-th derivative jumps
     T px[K + 1], py[K + 1], wx[LMAX + 1], wy[LMAX + 1];
@@ -262,12 +259,7 @@ struct Stage2D {
         hy *= a.hy;
       }
     }
-    double my_rate = 0.0;
-    T my_rate_t = T(0);
-    bool my_ok = true;
-
-    if (active) {
-      const int strip = (int)(gw % a.nstrips), chunk = (int)(gw / a.nstrips);
+    {
       const int x = strip * STRIP_OUT - 2 + lane;
       const bool perx = a.bcx == BC_PERIODIC, pery = a.bcy == BC_PERIODIC;
       const int xc = perx ? ((x % nx) + nx) % nx : (x < 0 ? 0 : (x >= nx ? nx - 1 : x));
@@ -570,6 +562,21 @@ struct Stage2D {
         for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
       }
     }
+  }
+
+  // Single-instance stage: one warp per tile item, step control on the instance's DevScalars.
+  static __device__ void run(const Stage2DArgs& a, unsigned char* smem) {
+    const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
+    if (!ctl.run) return;
+    const int wib = threadIdx.x >> 5;
+    double* red = (double*)smem;                                  // 32 doubles for stage_end
+    T* ws = (T*)(smem + 256 + warp_bytes() * wib);
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    double my_rate = 0.0;
+    T my_rate_t = T(0);
+    bool my_ok = true;
+    if (gw < (long long)a.nstrips * a.nchunks)
+      item(a, ctl.dt, (int)(gw % a.nstrips), (int)(gw / a.nstrips), ws, my_rate, my_rate_t, my_ok);
     if constexpr (PR::MIXED) my_rate = (double)my_rate_t;
     stage_end(a.sc, a.stage, my_rate, my_ok, red);
   }
