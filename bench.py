@@ -109,10 +109,109 @@ def dist_setup():
     return world, rank, local
 
 
-def make_solver(N, precision, nx, seed, stream):
+def aggregate(torch, dist, ms_local, work_local, world, device):
+    """Whole-job throughput over replicas: the work of all ranks divided by the slowest rank's time
+    (max over ranks of the timed region). Returns (value, ms_max)."""
+    if world == 1:
+        return work_local / (ms_local * 1e-3), ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work_local], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(w.item()) / (ms_max * 1e-3), ms_max
+
+
+def accepted(name):
+    out = []
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                sd, ok, _ = line.split()
+                if int(ok):
+                    out.append(int(sd))
+    except OSError:
+        pass
+    return out or [1]
+
+
+def make_instance(N, I, spec, stream, tiles):
+    """One batched instance (FP32 form) from inputs.batched_specs."""
+    kind, n, k = spec["kind"], spec["n"], spec["k"]
+    H, W = tiles.get(k, (0, 0)) if spec["dim"] == 2 else (0, 0)
+    if spec["dim"] == 1:
+        bc = (N.BC_OUTFLOW,) * 4 if kind == "riemann1d" else (N.BC_PERIODIC,) * 4
+        s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=bc, precision=N.PREC_FP32_MIXED, stream=stream)
+        if kind == "riemann1d":
+            s.set_initial(N.IC_RIEMANN1D, I.riemann1d_params(spec["seed"]))
+        else:
+            s.set_initial(N.IC_ENTROPY1D, [1.0, 0.2, 2 * math.pi, 1.0, 1.0])
+    elif kind == "quadrant2d":
+        s = N.Solver(dim=2, nx=n, ny=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4,
+                     precision=N.PREC_FP32_MIXED, stream=stream, tile_rows=H, tile_warps=W)
+        s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(spec["seed"]))
+    else:
+        s = N.Solver(dim=2, nx=n, ny=n, x0=0.0, x1=10.0, y0=-5.0, y1=5.0, k=k, eq=N.EQ_EULER,
+                     bc=(N.BC_PERIODIC,) * 4, precision=N.PREC_FP32_MIXED, stream=stream, tile_rows=H,
+                     tile_warps=W)
+        s.set_initial(N.IC_VORTEX2D, [5.0, 0.0, 5.0, 0.0])
+    return s
+
+
+def run_batched(torch, N, stream, steps, n_inst):
+    """S2: n_inst uneven instances (inputs.batched_specs), each advanced `steps` steps by dg_batch_run
+    (one graph-captured work-list launch per class and stage); autotuned 2D tiles per degree."""
+    from paper_2407_19169_gb300 import inputs as I
+    from paper_2407_19169_gb300 import tuning
+    specs = I.batched_specs(n=n_inst, riemann_seeds=accepted("riemann1d_seeds.txt"),
+                            quadrant_seeds=accepted("quadrant_seeds.txt"))
+    tiles = {k: tuning.tune_2d(256, 256, k=k) for k in (1, 2, 3)}
+    t0 = time.perf_counter()
+    inst = [make_instance(N, I, sp, stream.cuda_stream, tiles) for sp in specs]
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    dofs = [x.size for x in inst]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = inst[0].kernel_launches()
+    e0.record(stream)
+    st = N.batch_run(inst, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = inst[0].kernel_launches() - l0
+    done = [x.sync() for x in inst]
+    ok = [d[0] == 0 and d[2] == steps for d in done]
+    work = sum(3.0 * d * steps for d, o in zip(dofs, ok) if o)
+    for x in inst:
+        x.close()
+    return {"value": work / (ms * 1e-3), "unit": UNIT, "instances": n_inst, "steps_each": steps,
+            "total_dofs": int(sum(dofs)), "ms": ms, "failed_instances": int(len(ok) - sum(ok)),
+            "status": st, "setup_s": setup_s, "tiles_by_degree": {str(k): list(v) for k, v in tiles.items()},
+            "gpu_launches": launches, "dtype": "f32+df64"}
+
+
+def run_served(N, stream, rate, n_req, budget):
+    """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching."""
+    from paper_2407_19169_gb300 import serve as S
+    reqs = S.poisson_requests(rate=rate, n=n_req, seed=5, seeds=accepted("quadrant_seeds.txt"))
+    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    results, stats = eng.run(reqs)
+    wall = time.perf_counter() - t0
+    out = S.summarize(results, wall)
+    out.update({"rate_per_s": rate, "requests": n_req, "budget_gb": budget / 1e9, **stats,
+                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form"})
+    return out
+
+
+def make_solver(N, precision, nx, seed, stream, tile=(0, 0)):
     from paper_2407_19169_gb300 import inputs as I
     s = N.Solver(dim=2, nx=nx, ny=nx, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(N.BC_OUTFLOW,) * 4, k=2,
-                 eq=N.EQ_EULER, filter=1, cfl=0.1, gamma=1.4, precision=precision, stream=stream)
+                 eq=N.EQ_EULER, filter=1, cfl=0.1, gamma=1.4, precision=precision, stream=stream,
+                 tile_rows=tile[0], tile_warps=tile[1])
     s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(seed))
     return s
 
@@ -208,6 +307,14 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-tune", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--batched-instances", type=int, default=512)
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--skip-served", action="store_true")
+    ap.add_argument("--served-rate", type=float, default=10.0)
+    ap.add_argument("--served-requests", type=int, default=12)
+    ap.add_argument("--served-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.mesh == 2048:
         args.warmup = 3
@@ -241,8 +348,12 @@ def main():
     nx = args.mesh
     out = {}
 
-    # ---- headline: the FP32 form, inputs resident ----
-    s32 = make_solver(N, N.PREC_FP32_MIXED, nx, seed, sh)
+    # ---- headline: the FP32 form, inputs resident, autotuned tile shape ----
+    tile = (0, 0)
+    if not args.skip_tune:
+        from paper_2407_19169_gb300 import tuning
+        tile = tuning.tune_2d(nx, nx, k=2)
+    s32 = make_solver(N, N.PREC_FP32_MIXED, nx, seed, sh, tile)
     nv, nm, nc = s32.shape
     ndof = nv * nm * nc
     s32.advance_steps(args.warmup)
@@ -255,7 +366,7 @@ def main():
     # ---- the plain FP64 path ----
     fp64 = None
     if not args.skip_fp64:
-        s64 = make_solver(N, N.PREC_FP64, nx, seed, sh)
+        s64 = make_solver(N, N.PREC_FP64, nx, seed, sh, tile)
         s64.advance_steps(args.warmup)
         torch.cuda.synchronize()
         k64 = args.fp64_steps
@@ -291,14 +402,15 @@ def main():
     launch_ms = ms32 / (3 * args.steps)
     alg_bytes = (8.0 / 3.0) * state_bytes32          # 8 state moves per 3 stages
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    value = 3.0 * ndof * args.steps / (ms32 * 1e-3)
+    dist_mod = None
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms32], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        value = world * 3.0 * ndof * args.steps / (ms_max * 1e-3)
-        ms32 = ms_max
+        import torch.distributed as dist_mod
+    value, ms32 = aggregate(torch, dist_mod, ms32, 3.0 * ndof * args.steps, world, "cuda")
+
+    batched = None if args.skip_batched else run_batched(torch, N, stream, args.batched_steps,
+                                                         args.batched_instances)
+    served = None if args.skip_served else run_served(N, stream, args.served_rate, args.served_requests,
+                                                      args.served_budget_gb * 1e9)
     if rank != 0:
         return
     line = {
@@ -308,7 +420,8 @@ def main():
         "config": {"workload": WORKLOAD, "mesh": [nx, nx], "degree": 2, "basis": "Q2", "dofs": ndof,
                    "seed": seed, "precision": "FP32 stage arithmetic, cell averages double-float",
                    "l2": "inputs larger than L2 (state %.0f MB per buffer)" % (state_bytes32 / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tile": {"rows": tile[0], "warps": tile[1], "source": "autotuned" if tile[0] else "default"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": src,
                      "kernel": "stage2d_kernel<2,EULER,Q,FP32 form>", "launch_ms": launch_ms,
@@ -316,7 +429,10 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches32,
         "fp64": fp64,
+        "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": e2e,
+        "batched": batched,
+        "served": served,
     }
     if not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(128 if nx >= 128 else nx, args.cpu_seconds, seed)

@@ -106,3 +106,26 @@ WORKLOADS = {
     "vortex2d": dict(dim=2, x0=0.0, x1=10.0, y0=-5.0, y1=5.0, k=2, eq="euler", bc="periodic", T=10.0,
                      ic=("vortex2d", [5.0, 0.0, 5.0, 0.0])),
 }
+
+
+def batched_specs(n=512, seed=4, riemann_seeds=(1, 2, 3, 4), quadrant_seeds=(1, 4, 7, 8)):
+    """The batched workload: n uneven instances. Per instance: 1D or 2D with probability 1/2; 1D
+    cells log-uniform in [1e3, 1e6], 2D side log-uniform in [64, 1024] (both rounded to even, so a
+    Riemann split at 1/2 lies on a face); degree uniform in {1, 2, 3}; seeded Riemann data or the
+    smooth problem of that dimension (1D entropy wave, 2D vortex) with probability 1/2."""
+    g = SplitMix64(seed)
+    out = []
+    for i in range(n):
+        dim = 1 if g.uniform(0, 1) < 0.5 else 2
+        if dim == 1:
+            size = 2 * int(round(10 ** g.uniform(3.0, 6.0) / 2))
+        else:
+            size = 2 * int(round(2 ** g.uniform(6.0, 10.0) / 2))
+        k = 1 + min(int(g.uniform(0, 3)), 2)
+        riemann = g.uniform(0, 1) < 0.5
+        if dim == 1:
+            kind, s = ("riemann1d", riemann_seeds[i % len(riemann_seeds)]) if riemann else ("entropy1d", 0)
+        else:
+            kind, s = ("quadrant2d", quadrant_seeds[i % len(quadrant_seeds)]) if riemann else ("vortex2d", 0)
+        out.append(dict(dim=dim, n=size, k=k, kind=kind, seed=s))
+    return out

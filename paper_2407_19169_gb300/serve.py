@@ -1,0 +1,146 @@
+"""Served solves with continuous batching.
+
+Requests (2D Euler Q2 four-quadrant Riemann solves of different mesh sizes and end times) arrive
+as a Poisson stream. The engine keeps every admitted solve's state resident on the GPU and advances
+all of them together with dg_batch_run in chunks of a few steps; at every chunk boundary it retires
+the solves that reached their end time (each stops exactly at its own T) and admits waiting
+requests while the device-memory budget allows. Latency = completion time - arrival time.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+from . import _native as N
+from . import inputs as I
+
+SIDES = (128, 256, 512, 1024)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float      # seconds after the start of the session
+    side: int
+    T: float
+    seed: int
+
+
+def poisson_requests(rate, n, seed, seeds, sides=SIDES, t_range=(0.05, 0.25)):
+    """n requests with exponential inter-arrival times (mean 1/rate); side uniform in `sides`, end
+    time uniform in t_range, Riemann data from the screened seed list `seeds`."""
+    g = I.SplitMix64(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += -math.log(1.0 - g.uniform(0.0, 1.0)) / rate
+        side = sides[min(int(g.uniform(0, len(sides))), len(sides) - 1)]
+        T = g.uniform(*t_range)
+        out.append(Request(i, t, side, T, seeds[i % len(seeds)]))
+    return out
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    side: int
+    T: float
+    arrival: float
+    admitted: float
+    done: float
+    steps: int
+    dofs: int
+    status: int
+    state: object = None
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+
+class Engine:
+    """Continuous-batching loop over resident solves.
+
+    budget_bytes: device memory the admitted solves may hold together (dg_workspace_size each).
+    chunk_steps: steps per dg_batch_run call (the admission / retirement granularity).
+    """
+
+    def __init__(self, budget_bytes=120e9, chunk_steps=16, precision=N.PREC_FP32_MIXED, stream=None,
+                 keep_states=False, max_active=512):
+        self.budget = budget_bytes
+        self.chunk = chunk_steps
+        self.precision = precision
+        self.stream = stream
+        self.keep = keep_states
+        self.max_active = max_active
+
+    def _bytes(self, req):
+        return N.Solver.workspace_size(dim=2, nx=req.side, ny=req.side, bc=(N.BC_OUTFLOW,) * 4, k=2,
+                                       eq=N.EQ_EULER, precision=self.precision)
+
+    def _start(self, req):
+        s = N.Solver(dim=2, nx=req.side, ny=req.side, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
+                     bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER, precision=self.precision,
+                     stream=self.stream)
+        s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(req.seed))
+        s.set_target(req.T)
+        return s
+
+    def run(self, requests, clock=time.perf_counter):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active = []          # (request, solver, admitted time, bytes)
+        used = 0.0
+        results = []
+        peak_active = 0
+        peak_bytes = 0.0
+        t0 = clock()
+        now = lambda: clock() - t0  # noqa: E731
+        while pending or active:
+            # admission: arrived requests, in arrival order, while memory and slots allow
+            while pending and pending[0].arrival <= now() and len(active) < self.max_active:
+                need = self._bytes(pending[0])
+                if used + need > self.budget and active:
+                    break
+                req = pending.pop(0)
+                active.append((req, self._start(req), now(), need))
+                used += need
+            peak_active = max(peak_active, len(active))
+            peak_bytes = max(peak_bytes, used)
+            if not active:
+                time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
+                continue
+            st = N.batch_run([a[1] for a in active], self.chunk)
+            still = []
+            for req, s, adm, need in active:
+                status, t, steps = s.sync()
+                if status != 0 or t >= req.T:
+                    state = None
+                    if self.keep and status == 0:
+                        state = s.read_state()[0]
+                    else:
+                        s.mass()          # the solve's result summary reaches the host
+                    results.append(Result(req.rid, req.side, req.T, req.arrival, adm, now(), steps,
+                                          s.size, status, state))
+                    s.close()
+                    used -= need
+                else:
+                    still.append((req, s, adm, need))
+            active = still
+            del st
+        return results, {"peak_active": peak_active, "peak_bytes": peak_bytes}
+
+
+def summarize(results, wall):
+    lat = sorted(r.latency for r in results if r.status == 0)
+    if not lat:
+        return {"completed": 0}
+
+    def pct(p):
+        i = min(len(lat) - 1, max(0, int(math.ceil(p / 100.0 * len(lat))) - 1))
+        return lat[i]
+
+    dof_stage = sum(3.0 * r.dofs * r.steps for r in results if r.status == 0)
+    return {"completed": len(lat), "failed": sum(r.status != 0 for r in results),
+            "p50_s": pct(50), "p99_s": pct(99), "mean_s": sum(lat) / len(lat),
+            "throughput_solves_per_s": len(lat) / wall, "dof_stage_per_s": dof_stage / wall, "wall_s": wall}
