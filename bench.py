@@ -143,26 +143,28 @@ def make_instance(N, I, spec, stream, tiles):
     H, W = tiles.get(k, (0, 0)) if spec["dim"] == 2 else (0, 0)
     if spec["dim"] == 1:
         bc = (N.BC_OUTFLOW,) * 4 if kind == "riemann1d" else (N.BC_PERIODIC,) * 4
-        s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=bc, precision=N.PREC_FP32_MIXED, stream=stream)
+        s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=bc, precision=N.PREC_FP32_MIXED, stream=stream,
+                     positivity=1)
         if kind == "riemann1d":
             s.set_initial(N.IC_RIEMANN1D, I.riemann1d_params(spec["seed"]))
         else:
             s.set_initial(N.IC_ENTROPY1D, [1.0, 0.2, 2 * math.pi, 1.0, 1.0])
     elif kind == "quadrant2d":
         s = N.Solver(dim=2, nx=n, ny=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4,
-                     precision=N.PREC_FP32_MIXED, stream=stream, tile_rows=H, tile_warps=W)
+                     precision=N.PREC_FP32_MIXED, stream=stream, tile_rows=H, tile_warps=W, positivity=1)
         s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(spec["seed"]))
     else:
         s = N.Solver(dim=2, nx=n, ny=n, x0=0.0, x1=10.0, y0=-5.0, y1=5.0, k=k, eq=N.EQ_EULER,
                      bc=(N.BC_PERIODIC,) * 4, precision=N.PREC_FP32_MIXED, stream=stream, tile_rows=H,
-                     tile_warps=W)
+                     tile_warps=W, positivity=1)
         s.set_initial(N.IC_VORTEX2D, [5.0, 0.0, 5.0, 0.0])
     return s
 
 
 def run_batched(torch, N, stream, steps, n_inst):
     """S2: n_inst uneven instances (inputs.batched_specs), each advanced `steps` steps by dg_batch_run
-    (one graph-captured work-list launch per class and stage); autotuned 2D tiles per degree."""
+    (one graph-captured work-list launch per class and stage); autotuned 2D tiles per degree; the
+    positivity-preserving limiter after the filter, as the paper does for hard Riemann data."""
     from paper_2407_19169_gb300 import inputs as I
     from paper_2407_19169_gb300 import tuning
     specs = I.batched_specs(n=n_inst, riemann_seeds=accepted("riemann1d_seeds.txt"),
@@ -190,20 +192,20 @@ def run_batched(torch, N, stream, steps, n_inst):
     return {"value": work / (ms * 1e-3), "unit": UNIT, "instances": n_inst, "steps_each": steps,
             "total_dofs": int(sum(dofs)), "ms": ms, "failed_instances": int(len(ok) - sum(ok)),
             "status": st, "setup_s": setup_s, "tiles_by_degree": {str(k): list(v) for k, v in tiles.items()},
-            "gpu_launches": launches, "dtype": "f32+df64"}
+            "gpu_launches": launches, "dtype": "f32+df64", "positivity_limiter": True}
 
 
 def run_served(N, stream, rate, n_req, budget):
     """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching."""
     from paper_2407_19169_gb300 import serve as S
     reqs = S.poisson_requests(rate=rate, n=n_req, seed=5, seeds=accepted("quadrant_seeds.txt"))
-    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream)
+    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream, positivity=1)
     t0 = time.perf_counter()
     results, stats = eng.run(reqs)
     wall = time.perf_counter() - t0
     out = S.summarize(results, wall)
     out.update({"rate_per_s": rate, "requests": n_req, "budget_gb": budget / 1e9, **stats,
-                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form"})
+                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form", "positivity_limiter": True})
     return out
 
 
@@ -308,6 +310,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-tune", action="store_true")
+    ap.add_argument("--tile-rows", type=int, default=0, help="force the 2D tile rows (skips tuning)")
+    ap.add_argument("--tile-warps", type=int, default=0, help="force the warps per block")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=200)
@@ -349,8 +353,8 @@ def main():
     out = {}
 
     # ---- headline: the FP32 form, inputs resident, autotuned tile shape ----
-    tile = (0, 0)
-    if not args.skip_tune:
+    tile = (args.tile_rows, args.tile_warps)
+    if not args.skip_tune and not args.tile_rows:
         from paper_2407_19169_gb300 import tuning
         tile = tuning.tune_2d(nx, nx, k=2)
     s32 = make_solver(N, N.PREC_FP32_MIXED, nx, seed, sh, tile)

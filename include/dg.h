@@ -90,7 +90,11 @@ typedef struct {
  *             256 bytes; NULL = the library allocates
  *   tile_rows rows per warp in the 2D stage kernel, 0 = default
  *   tile_warps warps per thread block of the 2D stage kernel, 0 = default (both are tile-shape knobs
- *             for the autotuner; results do not depend on them) */
+ *             for the autotuner; results do not depend on them)
+ *   positivity Euler only: 1 = the positivity-preserving limiter of Zhang and Shu after the filter in
+ *             every stage (the paper applies it this way in Section 3.2), 0 = off (default): density
+ *             and pressure are kept >= min(1e-10, rho_bar, p_bar) at the volume and edge Gauss points
+ *             by scaling the modes l >= 1; cell averages are untouched */
 typedef struct {
   int enabled;
   double cfl;
@@ -103,6 +107,7 @@ typedef struct {
   size_t workspace_bytes;
   int tile_rows;
   int tile_warps;
+  int positivity;
 } dg_filter_params;
 
 typedef struct dg_solver dg_solver; /* opaque, library-owned */

@@ -36,7 +36,7 @@ class _Problem(C.Structure):
                 ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
                 ("bc", C.c_int * 4), ("k", C.c_int), ("basis", C.c_int), ("eq", C.c_int),
                 ("gamma", C.c_double), ("adv", C.c_double * 2), ("filter", C.c_int),
-                ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int)]
+                ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int), ("positivity", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -58,6 +58,7 @@ class Problem:
     cfl: float = 0.1
     nq: int = 0
     filter_dt_mode: int = 0
+    positivity: int = 0
 
     def c(self) -> _Problem:
         s = _Problem()
@@ -118,6 +119,7 @@ def lib():
             "orc_project": (I, [P, I, dp, I, I, dp]), "orc_max_rate": (D, [P, dp]),
             "orc_dt": (D, [P, dp, D, D]), "orc_residual": (None, [P, dp, dp]),
             "orc_filter": (None, [P, dp, D, dp]), "orc_filter_sigma": (None, [P, dp, dp]),
+            "orc_positivity": (None, [P, dp]),
             "orc_rk_stage": (None, [P, I, dp, dp, D, dp]), "orc_step": (I, [P, dp, D]),
             "orc_advance": (I, [P, dp, D, D, C.c_long, dp, C.POINTER(C.c_long)]),
             "orc_check_physical": (I, [P, dp]), "orc_mass": (None, [P, dp, dp]),
@@ -229,6 +231,14 @@ def filter(p: Problem, u, dt_: float) -> np.ndarray:  # noqa: A001 - the paper's
     pc = p.c()
     lib().orc_filter(C.byref(pc), _dp(u), float(dt_), _dp(out))
     return out
+
+
+def positivity(p: Problem, u) -> np.ndarray:
+    """Zhang–Shu positivity-preserving limiter applied to a copy of u."""
+    u = _arr(u).copy()
+    pc = p.c()
+    lib().orc_positivity(C.byref(pc), _dp(u))
+    return u
 
 
 def filter_sigma(p: Problem, u) -> np.ndarray:

@@ -62,6 +62,7 @@ typedef struct {
   int nq;                  /* Gauss points per direction for volume and edges (0 -> k+1) */
   int filter_dt_mode;      /* 0: exp(-sigma*dt) with the full step dt after every stage;
                               1: the stage's own effective step (dt, dt/4, 2dt/3) */
+  int positivity;          /* Euler: 1 = Zhang-Shu positivity-preserving limiter after the filter */
 } orc_problem;
 
 /* ---- basis (orc_basis.c) ---- */
@@ -86,6 +87,7 @@ double orc_max_rate(const orc_problem* p, const double* u);   /* 1D: max beta/h;
 double orc_dt(const orc_problem* p, const double* u, double t, double T);
 void   orc_residual(const orc_problem* p, const double* u, double* R);
 void   orc_filter(const orc_problem* p, const double* u, double dt, double* out);
+void   orc_positivity(const orc_problem* p, double* u);            /* Zhang-Shu limiter, in place */
 void   orc_filter_sigma(const orc_problem* p, const double* u, double* sigma); /* sigma^l per cell, l=0..lmax */
 void   orc_rk_stage(const orc_problem* p, int s, const double* un, const double* us, double dt, double* out);
 int    orc_step(const orc_problem* p, double* u, double dt);  /* one SSP-RK3 step in place; 0 = ok */

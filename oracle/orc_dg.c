@@ -396,6 +396,81 @@ void orc_filter(const orc_problem* p, const double* u, double dt, double* out) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Positivity-preserving limiter of Zhang and Shu (J. Comput. Phys. 229, 2010), applied after the */
+/* jump filter when the problem asks for it (the paper does so in Section 3.2).                   */
+/* Checked at every point where the scheme evaluates the cell polynomial: the volume Gauss points */
+/* and the Gauss points of the edges (1D: Gauss points and both ends).                           */
+/* ------------------------------------------------------------------------------------------ */
+static int pp_points(const orc_problem* p, const ctx_t* c, double* xi, double* eta) {
+  int n = 0;
+  if (p->dim == 1) {
+    for (int a = 0; a < c->nq; ++a) { xi[n] = c->xq[a]; eta[n++] = 0.0; }
+    xi[n] = -1.0; eta[n++] = 0.0;
+    xi[n] = 1.0; eta[n++] = 0.0;
+    return n;
+  }
+  for (int a = 0; a < c->nq; ++a)
+    for (int b = 0; b < c->nq; ++b) { xi[n] = c->xq[a]; eta[n++] = c->xq[b]; }
+  for (int g = 0; g < c->nq; ++g) {
+    xi[n] = -1.0; eta[n++] = c->xq[g];
+    xi[n] = 1.0; eta[n++] = c->xq[g];
+    xi[n] = c->xq[g]; eta[n++] = -1.0;
+    xi[n] = c->xq[g]; eta[n++] = 1.0;
+  }
+  return n;
+}
+
+static void pp_cell(const orc_problem* p, const ctx_t* c, double* u, long cell) {
+  double xi[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ], eta[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ];
+  const int np = pp_points(p, c, xi, eta);
+  double ubar[ORC_MAXNV];
+  for (int v = 0; v < c->nv; ++v) ubar[v] = U(u, v, 0, cell);
+  const double pbar = orc_pressure(p, ubar);
+  double eps = 1e-10;
+  if (ubar[0] < eps) eps = ubar[0];
+  if (pbar < eps) eps = pbar;
+  if (!(eps > 0.0)) return;                 /* inadmissible average: reported by the step */
+  /* density: theta_1 = (rho_bar - eps) / (rho_bar - rho_min) when rho_min < eps */
+  double rmin = ubar[0];
+  for (int i = 0; i < np; ++i) {
+    double val[ORC_MAXNV];
+    eval_cell(p, c, u, cell, xi[i], eta[i], val);
+    if (val[0] < rmin) rmin = val[0];
+  }
+  if (rmin < eps) {
+    const double th1 = (ubar[0] - eps) / (ubar[0] - rmin);
+    for (int m = 1; m < c->nm; ++m) U(u, 0, m, cell) *= th1;
+  }
+  /* pressure: theta_2 = min over points of t with p(u_bar + t (u(x) - u_bar)) = eps (bisection;
+   * the admissible set is convex, so p - eps changes sign once on [0, 1]) */
+  double th2 = 1.0;
+  for (int i = 0; i < np; ++i) {
+    double val[ORC_MAXNV];
+    eval_cell(p, c, u, cell, xi[i], eta[i], val);
+    if (orc_pressure(p, val) >= eps) continue;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      double w[ORC_MAXNV];
+      for (int v = 0; v < c->nv; ++v) w[v] = ubar[v] + mid * (val[v] - ubar[v]);
+      if (orc_pressure(p, w) >= eps) lo = mid; else hi = mid;
+    }
+    if (lo < th2) th2 = lo;
+  }
+  if (th2 < 1.0)
+    for (int v = 0; v < c->nv; ++v)
+      for (int m = 1; m < c->nm; ++m) U(u, v, m, cell) *= th2;
+}
+
+void orc_positivity(const orc_problem* p, double* u) {
+  if (p->eq != ORC_EQ_EULER) return;
+  ctx_t cc;
+  make_ctx(p, &cc);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (long cell = 0; cell < cc.ncell; ++cell) pp_cell(p, &cc, u, cell);
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Time stepping: third-order SSP Runge–Kutta in Shu–Osher form, Eq. (err_rk1), filter after   */
 /* each stage, Eq. (err_rk2).                                                                 */
 /* ------------------------------------------------------------------------------------------ */
@@ -420,6 +495,7 @@ void orc_rk_stage(const orc_problem* p, int s, const double* un, const double* u
   } else {
     memcpy(out, tmp, sizeof(double) * n);
   }
+  if (p->positivity) orc_positivity(p, out);     /* after the filter (Section 3.2) */
   free(L);
   free(tmp);
 }

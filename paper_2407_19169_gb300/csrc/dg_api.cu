@@ -227,6 +227,7 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
   s->basis = mesh->dim == 2 ? params->basis : DG_BASIS_Q;
   s->prec = params->precision == DG_PREC_FP64 ? PREC_F64 : PREC_F32M;
   s->filter_on = params->enabled ? 1 : 0;
+  s->positivity = (params->positivity && equation == DG_EQ_EULER) ? 1 : 0;
   s->cfl = params->cfl;
   s->gamma = params->gamma;
   s->ax = params->adv_speed[0];
@@ -467,6 +468,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.ax = s->ax;
       a.cfl = s->cfl;
       a.nwarps = s->nwarps1d;
+      a.positivity = s->positivity;
       a.sc = s->sc;
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     } else {
@@ -492,6 +494,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.H = s->H;
       a.nstrips = s->nstrips;
       a.nchunks = s->nchunks;
+      a.positivity = s->positivity;
       a.sc = s->sc;
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     }

@@ -27,7 +27,7 @@ struct BatchInst {
   DevScalars* sc;
   long long ncell;
   long long item0;     // first work item of this instance within its class
-  int nx, ny, bcx, bcy, H, nstrips, nchunks, filter_on;
+  int nx, ny, bcx, bcy, H, nstrips, nchunks, filter_on, positivity;
   double hx, hy, gamma, ax, ay, cfl;
 };
 
@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
     a.H = I.H;
     a.nstrips = I.nstrips;
     a.nchunks = I.nchunks;
+    a.positivity = I.positivity;
     a.sc = I.sc;
     const long long local = w - I.item0;
     double r = 0.0;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
     a.ax = I.ax;
     a.cfl = I.cfl;
     a.nwarps = I.nstrips;
+    a.positivity = I.positivity;
     a.sc = I.sc;
     double r = 0.0;
     T rt = T(0);
@@ -262,6 +264,7 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
       I.nstrips = s->dim == 2 ? s->nstrips : s->nwarps1d;
       I.nchunks = s->dim == 2 ? s->nchunks : 1;
       I.filter_on = s->filter_on;
+      I.positivity = s->positivity;
       I.hx = s->geom.hx;
       I.hy = s->geom.hy;
       I.gamma = s->gamma;

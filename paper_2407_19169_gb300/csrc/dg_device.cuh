@@ -250,6 +250,31 @@ __device__ __forceinline__ void avg_params(const T* ub, T gamma, T gm1, T ax, T 
   }
 }
 
+// ---- positivity-preserving limiter (Zhang & Shu 2010), Euler ----------------------------------
+// Pressure of a conservative state (1D: NV = 3, 2D: NV = 4).
+template <int NV, class T>
+__device__ __forceinline__ T pressure_of(const T* w, T gm1) {
+  if constexpr (NV == 3) return gm1 * (w[2] - T(0.5) * w[1] * w[1] / w[0]);
+  else return gm1 * (w[3] - T(0.5) * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+}
+
+// Largest t in [0, 1] with p(ub + t (w - ub)) >= eps, by bisection (the admissible set is convex,
+// so p - eps changes sign once on the segment; p(ub) >= eps, p(w) < eps on entry).
+template <int NV, class T>
+__device__ __noinline__ T pp_segment(const T* ub, const T* w, T eps, T gm1) {
+  T lo = T(0), hi = T(1);
+  const int iters = sizeof(T) == 8 ? 60 : 30;
+#pragma unroll 1
+  for (int it = 0; it < iters; ++it) {
+    const T mid = T(0.5) * (lo + hi);
+    T x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = ub[v] + mid * (w[v] - ub[v]);
+    if (pressure_of<NV>(x, gm1) >= eps) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // ---- double-float arithmetic (error-free transformations; Dekker / Knuth) -------------------
 struct df {
   float hi, lo;

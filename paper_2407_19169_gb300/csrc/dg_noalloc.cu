@@ -138,6 +138,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.ax = p->adv_speed[0];
       a.cfl = p->cfl;
       a.nwarps = nwarps;
+      a.positivity = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
       a.sc = sc;
       if (L.launch(&a, (unsigned)((nwarps + 3) / 4), 128, 256, st) != cudaSuccess) return DG_ERR_CUDA;
     }
@@ -179,6 +180,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.H = H;
       a.nstrips = nstrips;
       a.nchunks = nchunks;
+      a.positivity = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
       a.sc = sc;
       if (L.launch(&a, (unsigned)((nw + wpb - 1) / wpb), 32 * wpb, smem, st) != cudaSuccess) return DG_ERR_CUDA;
     }

@@ -7,7 +7,7 @@
 
 struct dg_solver {
   dg_mesh mesh;
-  int k, eq, dim, basis, prec, filter_on, H, warps_per_block;
+  int k, eq, dim, basis, prec, filter_on, H, warps_per_block, positivity;
   double cfl, gamma, ax, ay;
   dgk::AuxGeom geom;
   size_t ndof, sbytes;

@@ -31,6 +31,7 @@ struct Stage1DArgs {
   int filter_on;
   double gamma, ax, cfl;
   int nwarps;
+  int positivity;    // Euler: Zhang-Shu limiter after the filter
   DevScalars* sc;
 };
 
@@ -212,6 +213,9 @@ struct Stage1D {
           for (int v = 0; v < NV; ++v) ut[v][l] *= fac;
         }
       }
+      if constexpr (EQ == EQ_EULER) {
+        if (a.positivity && out_lane) positivity_limit(ut, gm1);
+      }
       if (out_lane) {
         ST::store(a.uout, a.ncell, xc, ut, ulo);
         if (!phys) my_ok = false;
@@ -221,6 +225,60 @@ struct Stage1D {
           const double r = (double)bx / a.h;
           my_rate = (r > my_rate || r != r) ? r : my_rate;
         }
+      }
+    }
+  }
+
+  // Zhang-Shu positivity-preserving limiter on one cell (after the filter, Section 3.2 of the
+  // paper), checked at the Gauss points and both ends; averages untouched.
+  static __device__ void positivity_limit(T (&ut)[NV][NM], T gm1) {
+    if constexpr (EQ == EQ_EULER) {
+      constexpr int NP = NQ + 2;
+      T ub[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ub[v] = ut[v][0];
+      const T pbar = pressure_of<NV>(ub, gm1);
+      T eps = T(1e-10);
+      eps = ub[0] < eps ? ub[0] : eps;
+      eps = pbar < eps ? pbar : eps;
+      if (!(eps > T(0))) return;
+      auto coef = [&](int i, int l) -> double {
+        return i < NQ ? GR::P(l, i) : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
+      };
+      T rmin = ub[0];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T r = T(0);
+#pragma unroll
+        for (int l = 0; l < NM; ++l) r += (T)coef(i, l) * ut[0][l];
+        rmin = r < rmin ? r : rmin;
+      }
+      if (rmin < eps) {
+        const T th1 = (ub[0] - eps) / (ub[0] - rmin);
+#pragma unroll
+        for (int l = 1; l < NM; ++l) ut[0][l] *= th1;
+      }
+      T th2 = T(1);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T x = T(0);
+#pragma unroll
+          for (int l = 0; l < NM; ++l) x += (T)coef(i, l) * ut[v][l];
+          w[v] = x;
+        }
+        if (pressure_of<NV>(w, gm1) < eps) {
+          const T t = pp_segment<NV>(ub, w, eps, gm1);
+          th2 = t < th2 ? t : th2;
+        }
+      }
+      if (th2 < T(1)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int l = 1; l < NM; ++l) ut[v][l] *= th2;
       }
     }
   }

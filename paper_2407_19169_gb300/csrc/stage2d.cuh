@@ -41,6 +41,7 @@ struct Stage2DArgs {
   double gamma, ax, ay, cfl;
   int H;             // rows per chunk
   int nstrips, nchunks;
+  int positivity;    // Euler: Zhang-Shu limiter after the filter
   DevScalars* sc;
 };
 
@@ -541,6 +542,7 @@ struct Stage2D {
 #pragma unroll
               for (int m = 1; m < NM; ++m) uo[v][m] *= fac[PP[m] + QQ[m]];
           }
+          if (a.positivity && out_lane) positivity_limit(uo, gm1);
           if (out_lane) {
             ST::store(a.uout, a.ncell, cell2, uo, lo);
             if (!phys2) my_ok = false;
@@ -560,6 +562,71 @@ struct Stage2D {
         phys2 = phys1;
 #pragma unroll
         for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
+      }
+    }
+  }
+
+  // Zhang-Shu positivity-preserving limiter on one cell (after the filter, as in Section 3.2 of the
+  // paper): density first (theta_1), then pressure (theta_2), checked at the volume and edge Gauss
+  // points where the scheme evaluates the polynomial. Cell averages are not touched.
+  static __device__ void positivity_limit(T (&uo)[NV][NM], T gm1) {
+    if constexpr (EQ == EQ_EULER) {
+      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
+      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
+      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
+      constexpr int NP = NQ * NQ + 4 * NQ;
+      T ub[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ub[v] = uo[v][0];
+      const T pbar = pressure_of<NV>(ub, gm1);
+      T eps = T(1e-10);
+      eps = ub[0] < eps ? ub[0] : eps;
+      eps = pbar < eps ? pbar : eps;
+      if (!(eps > T(0))) return;
+      auto coef = [&](int i, int m) -> double {
+        return i < NQ * NQ ? VE[i * NM + m]
+                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
+      };
+      T rmin = ub[0];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T r = T(0);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const double c = coef(i, m);
+          if (c != 0.0) r += (T)c * uo[0][m];
+        }
+        rmin = r < rmin ? r : rmin;
+      }
+      if (rmin < eps) {
+        const T th1 = (ub[0] - eps) / (ub[0] - rmin);
+#pragma unroll
+        for (int m = 1; m < NM; ++m) uo[0][m] *= th1;
+      }
+      T th2 = T(1);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T x = T(0);
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            const double c = coef(i, m);
+            if (c != 0.0) x += (T)c * uo[v][m];
+          }
+          w[v] = x;
+        }
+        if (pressure_of<NV>(w, gm1) < eps) {
+          const T t = pp_segment<NV>(ub, w, eps, gm1);
+          th2 = t < th2 ? t : th2;
+        }
+      }
+      if (th2 < T(1)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int m = 1; m < NM; ++m) uo[v][m] *= th2;
       }
     }
   }

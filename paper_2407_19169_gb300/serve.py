@@ -64,16 +64,19 @@ class Engine:
 
     budget_bytes: device memory the admitted solves may hold together (dg_workspace_size each).
     chunk_steps: steps per dg_batch_run call (the admission / retirement granularity).
+    positivity: the Zhang-Shu limiter after the filter (on by default: random four-quadrant data
+        reach near-vacuum states that the unlimited scheme cannot hold).
     """
 
     def __init__(self, budget_bytes=120e9, chunk_steps=16, precision=N.PREC_FP32_MIXED, stream=None,
-                 keep_states=False, max_active=512):
+                 keep_states=False, max_active=512, positivity=1):
         self.budget = budget_bytes
         self.chunk = chunk_steps
         self.precision = precision
         self.stream = stream
         self.keep = keep_states
         self.max_active = max_active
+        self.positivity = positivity
 
     def _bytes(self, req):
         return N.Solver.workspace_size(dim=2, nx=req.side, ny=req.side, bc=(N.BC_OUTFLOW,) * 4, k=2,
@@ -82,7 +85,7 @@ class Engine:
     def _start(self, req):
         s = N.Solver(dim=2, nx=req.side, ny=req.side, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
                      bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER, precision=self.precision,
-                     stream=self.stream)
+                     stream=self.stream, positivity=self.positivity)
         s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(req.seed))
         s.set_target(req.T)
         return s

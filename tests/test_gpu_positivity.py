@@ -1,0 +1,59 @@
+"""The positivity-preserving limiter on the GPU against the oracle (both apply it after the filter
+in every stage), on data where it is active."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_19169_gb300 import _native as N
+from paper_2407_19169_gb300 import inputs as I
+
+from _helpers import rel_l1
+
+pytestmark = pytest.mark.gpu
+INF = float("inf")
+
+
+def _pair2d(n, k, precision=N.PREC_FP64):
+    p = O.Problem(dim=2, nx=n, ny=n, k=k, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, positivity=1)
+    s = N.Solver(dim=2, nx=n, ny=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4, positivity=1,
+                 precision=precision, tile_rows=8)
+    return p, s
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_quadrant_seed3_with_limiter_matches_oracle(k):
+    p, s = _pair2d(40, k)
+    u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(3))
+    s.write_state(u0)
+    s.advance_steps(60)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 60)
+    assert rel_l1(p, ug, uo) <= 1e-10
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_rough_1d_states_limiter_active(k):
+    p = O.Problem(dim=1, nx=70, k=k, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
+    s = N.Solver(dim=1, nx=70, k=k, eq=N.EQ_EULER, bc=(N.BC_PERIODIC,) * 4, positivity=1)
+    u0 = I.random_modal_state(p.shape, 71 + k, [(0.5, 1.0), (-0.2, 0.2), (1.0, 2.0)], high_scale=0.4,
+                              decay=0.6)
+    u0 = O.positivity(p, u0)                           # an admissible start
+    s.write_state(u0)
+    s.advance_steps(10)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 10)
+    assert rel_l1(p, ug, uo) <= 1e-10
+
+
+def test_fp32_form_survives_with_the_limiter():
+    s = N.Solver(dim=2, nx=128, ny=128, k=2, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4,
+                 precision=N.PREC_FP32_MIXED, positivity=1)
+    s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(3))
+    s.advance_to(0.1)
+    st, t, n = s.sync()
+    assert st == 0 and t == 0.1
+    m0 = None
+    u, _ = s.read_state()
+    assert np.isfinite(u).all()

@@ -15,7 +15,7 @@ def test_served_results_equal_alone_under_budget():
     reqs = S.poisson_requests(rate=400.0, n=8, seed=5, seeds=SEEDS, sides=(32, 64), t_range=(0.01, 0.04))
     one = N.Solver.workspace_size(dim=2, nx=64, ny=64, bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER,
                                   precision=N.PREC_FP32_MIXED)
-    eng = S.Engine(budget_bytes=2.5 * one, chunk_steps=8, keep_states=True)
+    eng = S.Engine(budget_bytes=2.5 * one, chunk_steps=8, keep_states=True, positivity=1)
     results, stats = eng.run(reqs)
     assert len(results) == len(reqs) and all(r.status == 0 for r in results)
     assert stats["peak_bytes"] <= 2.5 * one
@@ -23,7 +23,7 @@ def test_served_results_equal_alone_under_budget():
     for r in results:
         req = reqs[r.rid]
         alone = N.Solver(dim=2, nx=req.side, ny=req.side, bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER,
-                         precision=N.PREC_FP32_MIXED)
+                         precision=N.PREC_FP32_MIXED, positivity=1)
         alone.set_initial(N.IC_QUADRANT2D, I.quadrant_params(req.seed))
         alone.advance_to(req.T)
         ua, ta = alone.read_state()
