@@ -158,7 +158,8 @@ DG_API dg_status dg_step(dg_solver* s, double* dt_taken);
 DG_API dg_status dg_advance_to(dg_solver* s, double T, long long max_steps, long long* steps_taken);
 
 /* Enqueue nsteps unclipped steps on the solver's stream without synchronising (for timing and for
- * overlapping several solvers). Use dg_sync to wait and collect the status. */
+ * overlapping several solvers). Replaces any stop condition set by dg_set_target (T_end = +inf).
+ * Use dg_sync to wait and collect the status. */
 DG_API dg_status dg_advance_steps(dg_solver* s, long long nsteps);
 
 /* Set the device stop condition: stepping stops (further steps are no-ops) once t reaches T_end

@@ -238,10 +238,16 @@ struct Stage1D {
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = ut[v][0];
       const T pbar = pressure_of<NV>(ub, gm1);
-      T eps = T(1e-10);
+      // admissibility margins: 1e-10 in FP64 (as the oracle). In the FP32 form point values of rho
+      // and |m|^2 / (2 rho) lose digits to cancellation when rho(x) << rho_bar, so the margins are
+      // relative: rho(x) >= 1e-3 rho_bar and p(x) >= 1e-3 (rho_bar + E_bar), which keeps a limited
+      // point positive when the next stage re-evaluates it in a different order
+      T eps_r = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * ub[0];
+      T eps = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * (ub[0] + fabs(ub[NV - 1]));
+      eps_r = ub[0] < eps_r ? ub[0] : eps_r;
       eps = ub[0] < eps ? ub[0] : eps;
       eps = pbar < eps ? pbar : eps;
-      if (!(eps > T(0))) return;
+      if (!(eps > T(0)) || !(eps_r > T(0))) return;
       auto coef = [&](int i, int l) -> double {
         return i < NQ ? GR::P(l, i) : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
       };
@@ -253,8 +259,8 @@ struct Stage1D {
         for (int l = 0; l < NM; ++l) r += (T)coef(i, l) * ut[0][l];
         rmin = r < rmin ? r : rmin;
       }
-      if (rmin < eps) {
-        const T th1 = (ub[0] - eps) / (ub[0] - rmin);
+      if (rmin < eps_r) {
+        const T th1 = (ub[0] - eps_r) / (ub[0] - rmin);
 #pragma unroll
         for (int l = 1; l < NM; ++l) ut[0][l] *= th1;
       }

@@ -579,10 +579,16 @@ struct Stage2D {
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = uo[v][0];
       const T pbar = pressure_of<NV>(ub, gm1);
-      T eps = T(1e-10);
+      // admissibility margins: 1e-10 in FP64 (as the oracle). In the FP32 form point values of rho
+      // and |m|^2 / (2 rho) lose digits to cancellation when rho(x) << rho_bar, so the margins are
+      // relative: rho(x) >= 1e-3 rho_bar and p(x) >= 1e-3 (rho_bar + E_bar), which keeps a limited
+      // point positive when the next stage re-evaluates it in a different order
+      T eps_r = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * ub[0];
+      T eps = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * (ub[0] + fabs(ub[NV - 1]));
+      eps_r = ub[0] < eps_r ? ub[0] : eps_r;
       eps = ub[0] < eps ? ub[0] : eps;
       eps = pbar < eps ? pbar : eps;
-      if (!(eps > T(0))) return;
+      if (!(eps > T(0)) || !(eps_r > T(0))) return;
       auto coef = [&](int i, int m) -> double {
         return i < NQ * NQ ? VE[i * NM + m]
                            : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
@@ -598,8 +604,8 @@ struct Stage2D {
         }
         rmin = r < rmin ? r : rmin;
       }
-      if (rmin < eps) {
-        const T th1 = (ub[0] - eps) / (ub[0] - rmin);
+      if (rmin < eps_r) {
+        const T th1 = (ub[0] - eps_r) / (ub[0] - rmin);
 #pragma unroll
         for (int m = 1; m < NM; ++m) uo[0][m] *= th1;
       }
