@@ -528,17 +528,28 @@ int orc_step(const orc_problem* p, double* u, double dt) {
   return bad;
 }
 
-/* CFL rate from cell averages: 1D max_j beta_j / h; 2D max (beta^x/hx + beta^y/hy). */
+/* CFL rate from cell averages: 1D max_j beta_j / h; 2D max (beta^x/hx + beta^y/hy). With the
+ * positivity-preserving limiter on, the wave speeds at the limiter's points count as well: Zhang
+ * and Shu's positivity result for the cell averages needs the CFL bound on the largest of them. */
 double orc_max_rate(const orc_problem* p, const double* u) {
   ctx_t c;
   make_ctx(p, &c);
   double best = 0.0;
+  double xi[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ], eta[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ];
+  const int np = (p->positivity && p->eq == ORC_EQ_EULER) ? pp_points(p, &c, xi, eta) : 0;
   for (long cell = 0; cell < c.ncell; ++cell) {
     double ubar[ORC_MAXNV];
     for (int v = 0; v < c.nv; ++v) ubar[v] = u[((long)v * c.nm) * c.ncell + cell];
     double r = orc_wave_speed(p, 0, ubar) / c.hx;
     if (p->dim == 2) r += orc_wave_speed(p, 1, ubar) / c.hy;
     if (r > best || isnan(r)) best = r;
+    for (int i = 0; i < np; ++i) {
+      double val[ORC_MAXNV];
+      eval_cell(p, &c, u, cell, xi[i], eta[i], val);
+      double rp = orc_wave_speed(p, 0, val) / c.hx;
+      if (p->dim == 2) rp += orc_wave_speed(p, 1, val) / c.hy;
+      if (rp > best || isnan(rp)) best = rp;
+    }
   }
   return best;
 }

@@ -153,27 +153,65 @@ __device__ inline double avg_of(const AuxGeom& g, const void* st, int v, long lo
   return (double)a.x + (double)a.y;
 }
 
+// Coefficient (v, m) of cell c from either storage form.
+__device__ inline double coef_of(const AuxGeom& g, const void* st, int v, int m, long long c) {
+  if (m == 0) return avg_of(g, st, v, c);
+  if (g.prec == PREC_F64) return ((const double*)st)[((long long)v * g.nm + m) * g.ncell + c];
+  const float* bh = (const float*)((const char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+  return (double)bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c];
+}
+
+// CFL rate of one state: beta^x / hx (+ beta^y / hy).
+__device__ inline double state_rate(const AuxGeom& g, const double* ub, bool& phys) {
+  double bx, by, invH;
+  if (g.eq == EQ_EULER) {
+    if (g.dim == 1) avg_params<EQ_EULER, 1>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
+    else avg_params<EQ_EULER, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
+  } else if (g.eq == EQ_BURG) {
+    avg_params<EQ_BURG, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
+  } else {
+    avg_params<EQ_ADV, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
+  }
+  return bx / g.hx + (g.dim == 2 ? by / g.hy : 0.0);
+}
+
+// Max CFL rate over the cells' averages; with the positivity limiter also over its points (the
+// k+1 Gauss points per direction of the volume and the edges, 1D: Gauss points and both ends).
 __global__ void rate_kernel(const AuxGeom g, const void* st, DevScalars* sc, int slot) {
   __shared__ double red[32];
   double r = 0.0;
   bool ok = true;
+  const int nq = g.k + 1;
+  const int npt = !g.pp ? 0 : (g.dim == 1 ? nq + 2 : nq * nq + 4 * nq);
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double ub[4];
     for (int v = 0; v < g.nv; ++v) ub[v] = avg_of(g, st, v, c);
-    double bx, by, invH;
     bool phys;
-    if (g.eq == EQ_EULER) {
-      if (g.dim == 1) avg_params<EQ_EULER, 1>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
-      else avg_params<EQ_EULER, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
-    } else if (g.eq == EQ_BURG) {
-      avg_params<EQ_BURG, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
-    } else {
-      avg_params<EQ_ADV, 2>(ub, g.gamma, g.gamma - 1.0, g.ax, g.ay, bx, by, invH, phys);
-    }
-    double rc = bx / g.hx + (g.dim == 2 ? by / g.hy : 0.0);
+    double rc = state_rate(g, ub, phys);
     r = (rc > r || rc != rc) ? rc : r;
     ok = ok && phys;
+    for (int i = 0; i < npt; ++i) {
+      double xi, eta = 0.0;
+      if (g.dim == 1) {
+        xi = i < nq ? c_gx[nq][i] : (i == nq ? -1.0 : 1.0);
+      } else if (i < nq * nq) {
+        xi = c_gx[nq][i / nq];
+        eta = c_gx[nq][i % nq];
+      } else {
+        const int e = (i - nq * nq) & 3, gq = (i - nq * nq) >> 2;
+        xi = e == 0 ? -1.0 : (e == 1 ? 1.0 : c_gx[nq][gq]);
+        eta = e == 2 ? -1.0 : (e == 3 ? 1.0 : c_gx[nq][gq]);
+      }
+      double w[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int m = 0; m < g.nm; ++m) {
+        const double phi = leg(g.mp[m], xi) * (g.dim == 2 ? leg(g.mq[m], eta) : 1.0);
+        for (int v = 0; v < g.nv; ++v) w[v] += phi * coef_of(g, st, v, m, c);
+      }
+      bool pphys;
+      const double rp = state_rate(g, w, pphys);
+      r = (rp > r || rp != rp) ? rp : r;
+    }
   }
   r = warp_max(r);
   const unsigned bad = __ballot_sync(0xffffffffu, !ok);

@@ -112,6 +112,7 @@ static void fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filt
   g.gamma = p->gamma;
   g.ax = p->adv_speed[0];
   g.ay = p->adv_speed[1];
+  g.pp = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
   int idx = 0;
   if (m->dim == 1) {
     for (int l = 0; l <= k; ++l) { g.mp[l] = l; g.mq[l] = 0; }

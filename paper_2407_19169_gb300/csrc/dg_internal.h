@@ -28,6 +28,7 @@ struct AuxGeom {
   long long ncell;
   double x0, y0, hx, hy, gamma, ax, ay;
   int mp[16], mq[16];  // (p, q) of each mode
+  int pp;              // Euler with the positivity limiter: the CFL rate also takes the limiter's points
 };
 
 cudaError_t aux_init_tables();  // copy Gauss rules to constant memory of the current device

@@ -98,6 +98,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
   g.eq = eq;
   g.basis = basis;
   g.prec = PREC_F64;
+  g.pp = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
   g.nv = nv;
   g.nm = nm;
   g.ncell = ncell;

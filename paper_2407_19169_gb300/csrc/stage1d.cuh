@@ -221,12 +221,47 @@ struct Stage1D {
         if (!phys) my_ok = false;
         if constexpr (PR::MIXED) {
           my_rate_t = nan_max(bx * inv_h, my_rate_t);
+          if (a.positivity) my_rate_t = nan_max(point_rate(ut, gam, gm1, a.h), my_rate_t);
         } else {
           const double r = (double)bx / a.h;
           my_rate = (r > my_rate || r != r) ? r : my_rate;
+          if (a.positivity) {
+            const double rp = (double)point_rate(ut, gam, gm1, a.h);
+            my_rate = (rp > my_rate || rp != rp) ? rp : my_rate;
+          }
         }
       }
     }
+  }
+
+  // Max CFL rate beta / h over the positivity limiter's points of one cell (Gauss points and both
+  // ends): with the limiter on, Zhang and Shu's positivity result for the averages needs the CFL
+  // bound on the wave speeds at those points.
+  static __device__ T point_rate(const T (&ut)[NV][NM], T gam, T gm1, double h) {
+    T best = T(0);
+    if constexpr (EQ == EQ_EULER) {
+      constexpr int NP = NQ + 2;
+      const T th = (T)h;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T x = T(0);
+#pragma unroll
+          for (int l = 0; l < NM; ++l) {
+            const double c = i < NQ ? GR::P(l, i) : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
+            x += (T)c * ut[v][l];
+          }
+          w[v] = x;
+        }
+        T bx, by, invH;
+        bool ph;
+        avg_params<EQ, 1>(w, gam, gm1, T(0), T(0), bx, by, invH, ph);
+        best = nan_max(bx / th, best);
+      }
+    }
+    return best;
   }
 
   // Zhang-Shu positivity-preserving limiter on one cell (after the filter, Section 3.2 of the

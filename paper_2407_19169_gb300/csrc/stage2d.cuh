@@ -549,9 +549,14 @@ struct Stage2D {
             if constexpr (PR::MIXED) {
               const T r = bx2 * inv_hx + by2 * inv_hy;
               my_rate_t = nan_max(r, my_rate_t);
+              if (a.positivity) my_rate_t = nan_max(point_rate(uo, gam, gm1, a.hx, a.hy), my_rate_t);
             } else {
               const double r = (double)bx2 / a.hx + (double)by2 / a.hy;
               my_rate = (r > my_rate || r != r) ? r : my_rate;
+              if (a.positivity) {
+                const double rp = (double)point_rate(uo, gam, gm1, a.hx, a.hy);
+                my_rate = (rp > my_rate || rp != rp) ? rp : my_rate;
+              }
             }
           }
         }
@@ -564,6 +569,41 @@ struct Stage2D {
         for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
       }
     }
+  }
+
+  // Max CFL rate beta^x / hx + beta^y / hy over the positivity limiter's points of one cell: with
+  // the limiter on, Zhang and Shu's positivity result for the averages needs the CFL bound on the
+  // wave speeds at those points, not only at the average.
+  static __device__ T point_rate(const T (&uo)[NV][NM], T gam, T gm1, double hx, double hy) {
+    T best = T(0);
+    if constexpr (EQ == EQ_EULER) {
+      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
+      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
+      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
+      constexpr int NP = NQ * NQ + 4 * NQ;
+      const T thx = (T)hx, thy = (T)hy;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T x = T(0);
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            const double c = i < NQ * NQ ? VE[i * NM + m]
+                                         : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m]
+                                                                 : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
+            if (c != 0.0) x += (T)c * uo[v][m];
+          }
+          w[v] = x;
+        }
+        T bx, by, invH;
+        bool ph;
+        avg_params<EQ, 2>(w, gam, gm1, T(0), T(0), bx, by, invH, ph);
+        best = nan_max(bx / thx + by / thy, best);
+      }
+    }
+    return best;
   }
 
   // Zhang-Shu positivity-preserving limiter on one cell (after the filter, as in Section 3.2 of the

@@ -83,3 +83,29 @@ def test_quadrant_riemann_needs_the_limiter():
     p1 = O.Problem(**base, positivity=1)
     u, t, n = O.advance(p1, O.project(p1, O.IC_QUADRANT2D, prm), 0.0, 0.1)
     assert t == 0.1 and O.check_physical(p1, u)
+
+
+def test_rate_takes_the_limiters_points_closed_form():
+    # rho = 1 + 0.6 P_1 at rest with constant E: p = 0.4 E everywhere and the sound speed
+    # sqrt(gamma p / rho) is largest where rho is smallest, at the left end (rho = 0.4).
+    h = 0.1
+    on = O.Problem(dim=1, nx=1, x0=0.0, x1=h, k=1, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
+    off = O.Problem(dim=1, nx=1, x0=0.0, x1=h, k=1, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=0)
+    u = np.zeros(on.shape)
+    u[0, :, 0] = [1.0, 0.6]
+    u[2, 0, 0] = 2.5
+    assert O.max_rate(off, u) == pytest.approx(np.sqrt(1.4 * 1.0 / 1.0) / h, rel=1e-14)
+    assert O.max_rate(on, u) == pytest.approx(np.sqrt(1.4 * 1.0 / 0.4) / h, rel=1e-14)
+
+
+def test_rate_2d_corner_edge_point():
+    # 2D: rho = 1 + 0.3 P_1(x) + 0.3 P_1(y) at rest, E = 2.5: on the edges the Gauss points of the
+    # left/bottom edges reach rho = 1 - 0.3 - 0.3 / sqrt(3); the volume points stay above that.
+    on = O.Problem(dim=2, nx=1, ny=1, x0=0.0, x1=0.1, y0=0.0, y1=0.2, k=1, eq=O.EQ_EULER,
+                   bc=(O.BC_PERIODIC,) * 4, positivity=1)
+    u = np.zeros(on.shape)
+    u[0, 0, 0], u[0, 1, 0], u[0, 2, 0] = 1.0, 0.3, 0.3     # modes (0,0), (1,0), (0,1)
+    u[3, 0, 0] = 2.5
+    rmin = 1.0 - 0.3 - 0.3 / np.sqrt(3.0)
+    c = np.sqrt(1.4 * 1.0 / rmin)
+    assert O.max_rate(on, u) == pytest.approx(c / 0.1 + c / 0.2, rel=1e-14)
