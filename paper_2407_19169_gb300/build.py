@@ -15,8 +15,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
 UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "dg_noalloc.cu", "dg_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-fvisibility=hidden"]
+# -prec-div=false / -prec-sqrt=false: single-precision division and square root by the hardware
+# approximations (a couple of ulp). They act only on FP32 arithmetic (the FP32 form's stage math);
+# FP64 and the double-float cell averages are untouched.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-prec-div=false", "-prec-sqrt=false",
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
 
 def _nvcc() -> str:
@@ -28,7 +31,7 @@ def _nvcc() -> str:
 
 def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + \
-        [os.path.join(os.path.dirname(HERE), "include", "dg.h")]
+        [os.path.join(os.path.dirname(HERE), "include", "dg.h"), os.path.abspath(__file__)]
 
 
 def _stale(obj: str) -> bool:

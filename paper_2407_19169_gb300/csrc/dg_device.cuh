@@ -88,6 +88,25 @@ struct carr {
   __host__ __device__ constexpr V& operator[](int i) { return v[i]; }
 };
 
+// Compile-time loop: f(cint<0>{}), ..., f(cint<N-1>{}). Inside f the index is a constant
+// expression (decltype(i)::value), so table entries it selects are folded by the front end and
+// `if constexpr` can drop zero terms; nothing depends on the optimiser unrolling a loop.
+template <int I>
+struct cint {
+  static constexpr int value = I;
+};
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor_from(F& f) {
+  if constexpr (I < N) {
+    f(cint<I>{});
+    sfor_from<I + 1, N>(f);
+  }
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  sfor_from<0, N>(f);
+}
+
 template <int EQ, int DIM>
 struct NVars {
   static constexpr int value = EQ == EQ_EULER ? (DIM == 1 ? 3 : 4) : 1;
@@ -311,6 +330,35 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
   e = __fmaf_rn(a.lo, b, e);
   return df_fast_two_sum(p, e);
 }
+// Running double-float sum: each float term is added to hi by an error-free two-sum and the
+// rounding error (with the low parts of df terms and products) is collected in lo; one fast
+// two-sum renormalises at the end. The error is a few units of 2^-48 times the sum of the terms'
+// magnitudes, which is what conservation of the cell averages needs (the flux terms of a face are
+// formed bitwise alike on its two sides).
+struct df_acc {
+  float hi, lo;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add(df x) {
+    add(x.hi);
+    lo = __fadd_rn(lo, x.lo);
+  }
+  // + a * b: a.hi * b exactly as p + e (FMA), a.lo * b rounded
+  __device__ __forceinline__ void add_prod(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ df result() const { return df_fast_two_sum(hi, lo); }
+};
+
 __host__ __device__ inline df df_from_double(double x) {
   float hi = (float)x;
   float lo = (float)(x - (double)hi);

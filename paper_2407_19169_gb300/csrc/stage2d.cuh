@@ -106,6 +106,93 @@ struct Store {
   }
 };
 
+// Compile-time tables of the tensor-product sum factorisation for degree K, basis BASIS (P^k drops
+// the modes p + q > k). All are evaluated by the compiler front end and read only in constant
+// expressions, so every coefficient the kernels multiply by is an immediate.
+template <int K, int BASIS>
+struct Tab2DBuild {
+  using MB = Modes<K, BASIS>;
+  using GR = GaussRule<K + 1>;
+  static constexpr int NQ = K + 1;
+  static constexpr int NM = MB::NM;
+
+  static constexpr carr<int, (K + 1) * (K + 1)> mi() {
+    carr<int, (K + 1) * (K + 1)> t{};
+    for (int i = 0; i < (K + 1) * (K + 1); ++i) t[i] = -1;
+    for (int m = 0; m < NM; ++m) t[MB::p(m) * (K + 1) + MB::q(m)] = m;
+    return t;
+  }
+  static constexpr carr<int, NM> pq(int which) {
+    carr<int, NM> t{};
+    for (int m = 0; m < NM; ++m) t[m] = which == 0 ? MB::p(m) : MB::q(m);
+    return t;
+  }
+  // [l * NQ + g]: P_l(x_g) (0), w_g P_l(x_g) (1), w_g P_l'(x_g) (2)
+  static constexpr carr<double, (K + 1) * NQ> gauss(int which) {
+    carr<double, (K + 1) * NQ> t{};
+    for (int l = 0; l <= K; ++l)
+      for (int g = 0; g < NQ; ++g)
+        t[l * NQ + g] = which == 0 ? GR::P(l, g) : (which == 1 ? GR::w(g) * GR::P(l, g) : GR::w(g) * GR::dP(l, g));
+    return t;
+  }
+  // [l * (K + 1) + r]: P_l^{(r)}(+1), zero for r > l
+  static constexpr carr<double, (K + 1) * (K + 1)> ends() {
+    carr<double, (K + 1) * (K + 1)> t{};
+    for (int l = 0; l <= K; ++l)
+      for (int r = 0; r <= K; ++r) t[l * (K + 1) + r] = dend(1, l, r);
+    return t;
+  }
+  static constexpr carr<double, NM> minv() {
+    carr<double, NM> t{};
+    for (int m = 0; m < NM; ++m) t[m] = 0.5 * (2 * MB::p(m) + 1) * (2 * MB::q(m) + 1);
+    return t;
+  }
+};
+
+template <int K, int BASIS>
+struct Tab2D {
+  using B = Tab2DBuild<K, BASIS>;
+  static constexpr int NQ = K + 1;
+  static constexpr int NM = B::NM;
+  static constexpr carr<int, (K + 1) * (K + 1)> MIX = B::mi();
+  static constexpr carr<int, NM> PP = B::pq(0);
+  static constexpr carr<int, NM> QQ = B::pq(1);
+  static constexpr carr<double, (K + 1) * NQ> GP = B::gauss(0);
+  static constexpr carr<double, (K + 1) * NQ> WP = B::gauss(1);
+  static constexpr carr<double, (K + 1) * NQ> WD = B::gauss(2);
+  static constexpr carr<double, (K + 1) * (K + 1)> DE = B::ends();
+  static constexpr carr<double, NM> MINV = B::minv();
+
+  static constexpr bool has(int p, int q) { return p <= K && q <= K && MIX[p * (K + 1) + q] >= 0; }
+  // a mode (p, q) with q of parity `par` (p fixed) / p of parity `par` (q fixed), index >= 1
+  static constexpr bool any_q_par(int p, int par) {
+    for (int q = 1; q <= K; ++q)
+      if ((q & 1) == par && has(p, q)) return true;
+    return false;
+  }
+  static constexpr bool any_p_par(int q, int par) {
+    for (int p = 1; p <= K; ++p)
+      if ((p & 1) == par && has(p, q)) return true;
+    return false;
+  }
+  // sum_q u[p,q] P_q^{(a2)}(+1) has terms of parity par in q (q >= a2)
+  static constexpr bool hq(int p, int a2, int par) {
+    for (int q = a2; q <= K; ++q)
+      if ((q & 1) == par && has(p, q) && DE[q * (K + 1) + a2] != 0.0) return true;
+    return false;
+  }
+  // the x-polynomial H[p][a2] exists (some q >= a2 with mode (p, q))
+  static constexpr bool hh(int p, int a2) { return hq(p, a2, 0) || hq(p, a2, 1); }
+  // sum_p H[p][a2] P_p^{(a1)}(+1) has terms of parity par in p
+  static constexpr bool hp(int a1, int a2, int par) {
+    for (int p = a1; p <= K; ++p)
+      if ((p & 1) == par && hh(p, a2) && DE[p * (K + 1) + a1] != 0.0) return true;
+    return false;
+  }
+  // derivative multi-indices alpha = (a1, a2) that can be nonzero
+  static constexpr bool alpha_ok(int a1, int a2) { return BASIS == BASIS_Q ? true : a1 + a2 <= K; }
+};
+
 template <int K, int EQ, int BASIS, class PR>
 struct Stage2D {
   using T = typename PR::T;
@@ -118,13 +205,13 @@ struct Stage2D {
   static constexpr int NME = NM + (PR::MIXED ? 1 : 0);  // slot words per variable (+ mode-0 low word)
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
+  using TB = Tab2D<K, BASIS>;
 
   // per-warp shared memory: 3 row slots of u~ plus the partial damping Q[v][l-1] of one row
   static constexpr size_t warp_bytes() { return sizeof(T) * (3 * NV * NME + NV * LMAX) * 32; }
   static constexpr size_t slot_bytes_per_warp() { return warp_bytes(); }
 
-  // ---- compile-time tables (evaluated by the front end) ----
-  // mode degrees and total degree l = p + q
+  // ---- compile-time tables of the positivity limiter's points (evaluated by the front end) ----
   __host__ __device__ static constexpr carr<int, NM> tab_p() {
     carr<int, NM> t{};
     for (int m = 0; m < NM; ++m) t[m] = MB::p(m);
@@ -151,41 +238,12 @@ struct Stage2D {
         for (int m = 0; m < NM; ++m) t[(sd * NQ + g) * NM + m] = dend(sd, MB::p(m), 0) * GR::P(MB::q(m), g);
     return t;
   }
-  // volume point values P_p(x_a) P_q(x_b) and the weighted test-function derivatives
-  __host__ __device__ static constexpr carr<double, NQ * NQ * NM> tab_vol(int which) {
+  // volume point values P_p(x_a) P_q(x_b)
+  __host__ __device__ static constexpr carr<double, NQ * NQ * NM> tab_vol(int) {
     carr<double, NQ * NQ * NM> t{};
     for (int qa = 0; qa < NQ; ++qa)
       for (int qb = 0; qb < NQ; ++qb)
-        for (int m = 0; m < NM; ++m) {
-          const int pp = MB::p(m), qq = MB::q(m);
-          const double w = GR::w(qa) * GR::w(qb);
-          double v = 0.0;
-          if (which == 0) v = GR::P(pp, qa) * GR::P(qq, qb);
-          if (which == 1) v = w * GR::dP(pp, qa) * GR::P(qq, qb);
-          if (which == 2) v = w * GR::P(pp, qa) * GR::dP(qq, qb);
-          t[(qa * NQ + qb) * NM + m] = v;
-        }
-    return t;
-  }
-  // edge quadrature against the test function: vertical edges w_g P_q(x_g), horizontal w_g P_p(x_g)
-  __host__ __device__ static constexpr carr<double, NQ * NM> tab_face(int horizontal) {
-    carr<double, NQ * NM> t{};
-    for (int g = 0; g < NQ; ++g)
-      for (int m = 0; m < NM; ++m) t[g * NM + m] = GR::w(g) * GR::P(horizontal ? MB::p(m) : MB::q(m), g);
-    return t;
-  }
-  // corner derivative coefficients d^a1 P_p(sx) d^a2 P_q(sy), corner index c = 2 sx + sy
-  __host__ __device__ static constexpr carr<double, 4 * NA * NM> tab_corner() {
-    carr<double, 4 * NA * NM> t{};
-    for (int c = 0; c < 4; ++c)
-      for (int a = 0; a < NA; ++a)
-        for (int m = 0; m < NM; ++m)
-          t[(c * NA + a) * NM + m] = dend(c >> 1, MB::p(m), MB::a1(a)) * dend(c & 1, MB::q(m), MB::a2(a));
-    return t;
-  }
-  __host__ __device__ static constexpr carr<int, NA> tab_a(int which) {
-    carr<int, NA> t{};
-    for (int a = 0; a < NA; ++a) t[a] = which == 0 ? MB::a1(a) : MB::a2(a);
+        for (int m = 0; m < NM; ++m) t[(qa * NQ + qb) * NM + m] = GR::P(MB::p(m), qa) * GR::P(MB::q(m), qb);
     return t;
   }
 
@@ -197,17 +255,258 @@ struct Stage2D {
   static __device__ __forceinline__ T shfl_down_t(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ T shfl_up_t(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
 
-  // Traces of all variables at Gauss point g of one edge.
-  static __device__ __forceinline__ void trace_at(const T (&u)[NV][NM], const double* tab, int g, T (&tr)[NV]) {
+  // ---- sum factorisation on the tensor-product modes (all coefficients are immediates) ----
+  // Sums start at -0, the additive identity (-0 + x == x for every x), so their first add folds away.
+
+  // f[g] = sum_{l=0..K} c[l] P_l(x_g) at the NQ Gauss nodes. P_l has the parity of l and the nodes
+  // are symmetric, so f[g] = E(x_g) + O(x_g) and f[NQ-1-g] = E(x_g) - O(x_g) with E, O the even- and
+  // odd-degree parts; the middle node of an odd rule sees only E.
+  static __device__ __forceinline__ void gauss_values(const T (&c)[K + 1], T (&f)[NQ]) {
+    sfor<NQ / 2>([&](auto G) {
+      constexpr int g = decltype(G)::value;
+      T ev = c[0], od = T(-0.0);
+      sfor<K + 1>([&](auto L) {
+        constexpr int l = decltype(L)::value;
+        constexpr double w = TB::GP[l * NQ + g];
+        if constexpr (l >= 1 && w != 0.0) {
+          if constexpr ((l & 1) != 0) od += c[l] * (T)w;
+          else ev += c[l] * (T)w;
+        }
+      });
+      f[g] = ev + od;
+      f[NQ - 1 - g] = ev - od;
+    });
+    if constexpr ((NQ & 1) != 0) {
+      T ev = c[0];
+      sfor<K + 1>([&](auto L) {
+        constexpr int l = decltype(L)::value;
+        constexpr double w = TB::GP[l * NQ + NQ / 2];
+        if constexpr (l >= 2 && (l & 1) == 0 && w != 0.0) ev += c[l] * (T)w;
+      });
+      f[NQ / 2] = ev;
+    }
+  }
+
+  // M[l] = sum_g w_g phi_l(x_g) F[g], l = 0..K, phi_l = P_l (DERIV = 0) or P_l' (DERIV = 1), from the
+  // node-pair sums F[g] + F[NQ-1-g] (phi_l even) and differences (phi_l odd). M[0] = 0 for DERIV = 1.
+  template <int DERIV>
+  static __device__ __forceinline__ void gauss_moments(const T (&F)[NQ], T (&M)[K + 1]) {
+    T s[NQ / 2], d[NQ / 2];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      T s = T(0);
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const double c = tab[g * NM + m];
-        if (c != 0.0) s += u[v][m] * (T)c;
+    for (int g = 0; g < NQ / 2; ++g) {
+      s[g] = F[g] + F[NQ - 1 - g];
+      d[g] = F[g] - F[NQ - 1 - g];
+    }
+    sfor<K + 1>([&](auto L) {
+      constexpr int l = decltype(L)::value;
+      constexpr bool even = ((l + DERIV) & 1) == 0;
+      T acc = T(-0.0);
+      sfor<NQ / 2>([&](auto G) {
+        constexpr int g = decltype(G)::value;
+        constexpr double w = DERIV ? TB::WD[l * NQ + g] : TB::WP[l * NQ + g];
+        if constexpr (w != 0.0) {
+          if constexpr (even) acc += s[g] * (T)w;
+          else acc += d[g] * (T)w;
+        }
+      });
+      if constexpr ((NQ & 1) != 0 && even) {
+        constexpr double w = DERIV ? TB::WD[l * NQ + NQ / 2] : TB::WP[l * NQ + NQ / 2];
+        if constexpr (w != 0.0) acc += F[NQ / 2] * (T)w;
       }
-      tr[v] = s;
+      M[l] = acc;
+    });
+  }
+
+  // Traces of u on the vertical edges xi = -1 (tl) and xi = +1 (tr) at the edge Gauss points:
+  // collapse p with P_p(+-1) = (+-1)^p, then evaluate the q-expansions at the nodes.
+  static __device__ __forceinline__ void edge_traces_v(const T (&u)[NV][NM], T (&tl)[NQ][NV], T (&tr)[NQ][NV]) {
+    sfor<NV>([&](auto V) {
+      constexpr int v = decltype(V)::value;
+      T cl[K + 1], cr[K + 1];
+      sfor<K + 1>([&](auto Q) {
+        constexpr int q = decltype(Q)::value;
+        T e = u[v][TB::MIX[q]], o = T(-0.0);
+        sfor<K + 1>([&](auto P) {
+          constexpr int p = decltype(P)::value;
+          constexpr int m = TB::MIX[p * (K + 1) + q];
+          if constexpr (p >= 1 && m >= 0) {
+            if constexpr ((p & 1) != 0) o += u[v][m];
+            else e += u[v][m];
+          }
+        });
+        if constexpr (TB::any_p_par(q, 1)) {
+          cr[q] = e + o;
+          cl[q] = e - o;
+        } else {
+          cr[q] = e;
+          cl[q] = e;
+        }
+      });
+      T fl[NQ], fr[NQ];
+      gauss_values(cl, fl);
+      gauss_values(cr, fr);
+#pragma unroll
+      for (int g = 0; g < NQ; ++g) {
+        tl[g][v] = fl[g];
+        tr[g][v] = fr[g];
+      }
+    });
+  }
+
+  // Traces of u on the horizontal edges eta = -1 (bot) and eta = +1 (top).
+  static __device__ __forceinline__ void edge_traces_h(const T (&u)[NV][NM], T (&bot)[NQ][NV], T (&top)[NQ][NV]) {
+    sfor<NV>([&](auto V) {
+      constexpr int v = decltype(V)::value;
+      T cb[K + 1], ct[K + 1];
+      sfor<K + 1>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        T e = u[v][TB::MIX[p * (K + 1)]], o = T(-0.0);
+        sfor<K + 1>([&](auto Q) {
+          constexpr int q = decltype(Q)::value;
+          constexpr int m = TB::MIX[p * (K + 1) + q];
+          if constexpr (q >= 1 && m >= 0) {
+            if constexpr ((q & 1) != 0) o += u[v][m];
+            else e += u[v][m];
+          }
+        });
+        if constexpr (TB::any_q_par(p, 1)) {
+          ct[p] = e + o;
+          cb[p] = e - o;
+        } else {
+          ct[p] = e;
+          cb[p] = e;
+        }
+      });
+      T fb[NQ], ft[NQ];
+      gauss_values(cb, fb);
+      gauss_values(ct, ft);
+#pragma unroll
+      for (int g = 0; g < NQ; ++g) {
+        bot[g][v] = fb[g];
+        top[g][v] = ft[g];
+      }
+    });
+  }
+
+  // Volume integral (F(u), grad phi) of one cell, sum-factorised column by column of Gauss points:
+  // for node x_a the q-coefficients C[q] = sum_p u[p,q] P_p(x_a) give the values at (x_a, y_b) for
+  // all b; the fluxes there are reduced to the moments Gx[q] = sum_b w_b P_q(y_b) f^x and
+  // Gy[q] = sum_b w_b P_q'(y_b) f^y, and acc[p,q] += w_a P_p'(x_a) sx Gx[q] + w_a P_p(x_a) sy Gy[q].
+  static __device__ __forceinline__ void volume(const T (&u)[NV][NM], T (&acc)[NV][NM], T sx, T sy, T gm1,
+                                                T ax, T ay) {
+    sfor<NQ>([&](auto A) {
+      constexpr int qa = decltype(A)::value;
+      T FX[NV][NQ], FY[NV][NQ];
+      {
+        T uq[NV][NQ];
+        sfor<NV>([&](auto V) {
+          constexpr int v = decltype(V)::value;
+          T c[K + 1];
+          sfor<K + 1>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            T s = u[v][TB::MIX[q]];
+            sfor<K + 1>([&](auto P) {
+              constexpr int p = decltype(P)::value;
+              constexpr int m = TB::MIX[p * (K + 1) + q];
+              constexpr double w = TB::GP[p * NQ + qa];
+              if constexpr (p >= 1 && m >= 0 && w != 0.0) s += u[v][m] * (T)w;
+            });
+            c[q] = s;
+          });
+          gauss_values(c, uq[v]);
+        });
+#pragma unroll
+        for (int qb = 0; qb < NQ; ++qb) {
+          T w[NV], fx[NV], fy[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w[v] = uq[v][qb];
+          flux2d_xy<EQ>(w, fx, fy, gm1, ax, ay);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            FX[v][qb] = fx[v];
+            FY[v][qb] = fy[v];
+          }
+        }
+      }
+      sfor<NV>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        T gx[K + 1], gy[K + 1];
+        gauss_moments<0>(FX[v], gx);
+        gauss_moments<1>(FY[v], gy);
+#pragma unroll
+        for (int q = 0; q <= K; ++q) {
+          gx[q] *= sx;
+          gy[q] *= sy;
+        }
+        sfor<NM>([&](auto Mi) {
+          constexpr int m = decltype(Mi)::value;
+          constexpr int p = TB::PP[m], q = TB::QQ[m];
+          constexpr double kx = TB::WD[p * NQ + qa], ky = TB::WP[p * NQ + qa];
+          if constexpr (kx != 0.0) acc[v][m] += (T)kx * gx[q];
+          if constexpr (q >= 1 && ky != 0.0) acc[v][m] += (T)ky * gy[q];
+        });
+      });
+    });
+  }
+
+  // eta-derivatives at the horizontal edges of one variable of a cell, for every x-mode p and order
+  // a2: H[p][a2] = sum_q w[p,q] P_q^{(a2)}(-1) (Hm) and (+1) (Hp), split by the parity of q since
+  // P_q^{(a2)}(-1) = (-1)^{q+a2} P_q^{(a2)}(+1). BOTH = false computes Hp only.
+  template <bool BOTH>
+  static __device__ __forceinline__ void eta_ends(const T (&w)[NM], T (&Hm)[K + 1][K + 1], T (&Hp)[K + 1][K + 1]) {
+    sfor<K + 1>([&](auto P) {
+      constexpr int p = decltype(P)::value;
+      sfor<K + 1>([&](auto A2_) {
+        constexpr int a2 = decltype(A2_)::value;
+        constexpr bool he = TB::hq(p, a2, 0), ho = TB::hq(p, a2, 1);
+        if constexpr (he || ho) {
+          T ev = T(-0.0), od = T(-0.0);
+          sfor<K + 1>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            constexpr int m = TB::MIX[p * (K + 1) + q];
+            constexpr double c = TB::DE[q * (K + 1) + a2];
+            if constexpr (m >= 0 && c != 0.0) {
+              if constexpr ((q & 1) != 0) od += w[m] * (T)c;
+              else ev += w[m] * (T)c;
+            }
+          });
+          if constexpr (he && ho) {
+            Hp[p][a2] = ev + od;
+            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? od - ev : ev - od;
+          } else if constexpr (he) {
+            Hp[p][a2] = ev;
+            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? -ev : ev;
+          } else {
+            Hp[p][a2] = od;
+            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? od : -od;
+          }
+        }
+      });
+    });
+  }
+
+  // d^(a1,a2) at xi = +1 (plus) and xi = -1 (minus) from one eta-edge row of H
+  template <int A1, int A2>
+  static __device__ __forceinline__ void xi_ends(const T (&H)[K + 1][K + 1], T& plus, T& minus) {
+    constexpr bool he = TB::hp(A1, A2, 0), ho = TB::hp(A1, A2, 1);
+    T ev = T(-0.0), od = T(-0.0);
+    sfor<K + 1>([&](auto P) {
+      constexpr int p = decltype(P)::value;
+      constexpr double c = TB::DE[p * (K + 1) + A1];
+      if constexpr (TB::hh(p, A2) && c != 0.0) {
+        if constexpr ((p & 1) != 0) od += H[p][A2] * (T)c;
+        else ev += H[p][A2] * (T)c;
+      }
+    });
+    if constexpr (he && ho) {
+      plus = ev + od;
+      minus = (A1 & 1) ? od - ev : ev - od;
+    } else if constexpr (he) {
+      plus = ev;
+      minus = (A1 & 1) ? -ev : ev;
+    } else {
+      plus = od;
+      minus = (A1 & 1) ? od : -od;
     }
   }
 
@@ -216,48 +515,42 @@ struct Stage2D {
   // and physicality are folded into my_rate (FP64 form) / my_rate_t (FP32 form) and my_ok.
   static __device__ void item(const Stage2DArgs& a, double dtd, int strip, int chunk, T* ws,
                               double& my_rate, T& my_rate_t, bool& my_ok) {
-    constexpr carr<int, NM> PP = tab_p();
-    constexpr carr<int, NM> QQ = tab_q();
-    constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
-    constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
-    constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
-    constexpr carr<double, NQ * NQ * NM> VX = tab_vol(1);
-    constexpr carr<double, NQ * NQ * NM> VY = tab_vol(2);
-    constexpr carr<double, NQ * NM> FXT = tab_face(0);
-    constexpr carr<double, NQ * NM> FYT = tab_face(1);
-    constexpr carr<double, 4 * NA * NM> CT = tab_corner();
-    constexpr carr<int, NA> A1 = tab_a(0);
-    constexpr carr<int, NA> A2 = tab_a(1);
+    constexpr carr<int, NM> PP = TB::PP;
+    constexpr carr<int, NM> QQ = TB::QQ;
+    constexpr carr<double, NM> MINV = TB::MINV;
 
     const T dt = (T)dtd;
     const int lane = threadIdx.x & 31;
     T* wq = ws + 3 * NV * NME * 32;                               // Q[v][l-1] of the next row to filter
     const int nx = a.nx, ny = a.ny;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax, ay = (T)a.ay;
-    const T inv_hx = (T)(1.0 / a.hx), inv_hy = (T)(1.0 / a.hy);
-    const T c1dt = (T)(a.c1 * dtd), c0 = (T)a.c0;
+    const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy, c1dt = a.c1 * dtd;
+    const T inv_hx = (T)ihx, inv_hy = (T)ihy;
+    // u~ = u + c0 (u^n - u) + c1 dt R: the edge and volume integrals enter through c1 dt / h
+    const T sx = (T)(c1dt * ihx), sy = (T)(c1dt * ihy), c0 = (T)a.c0;
     // double-float coefficients of the cell-average update (computed once, off the cell loop)
-    const df dfx = df_from_double(a.c1 * dtd * 0.5 / a.hx);
-    const df dfy = df_from_double(a.c1 * dtd * 0.5 / a.hy);
+    const df dfx = df_from_double(0.5 * c1dt * ihx);
+    const df dfy = df_from_double(0.5 * c1dt * ihy);
     const df dfc0 = df_from_double(a.c0);
-    // powers of 2/h for physical derivatives; weights m(m+1) h^m of the m-th derivative jumps
+    // powers of 2/h for physical derivatives; weights m(m+1) h^m of the m-th derivative jumps, with
+    // the 1/2 of the trapezoidal rule over an edge's two corners
     T px[K + 1], py[K + 1], wx[LMAX + 1], wy[LMAX + 1];
     {
-      double sx = 1.0, sy = 1.0;
+      const T hxT = (T)a.hx, hyT = (T)a.hy, tx = T(2) * inv_hx, ty = T(2) * inv_hy;
+      px[0] = py[0] = T(1);
 #pragma unroll
-      for (int r = 0; r <= K; ++r) {
-        px[r] = (T)sx;
-        py[r] = (T)sy;
-        sx *= 2.0 / a.hx;
-        sy *= 2.0 / a.hy;
+      for (int r = 1; r <= K; ++r) {
+        px[r] = px[r - 1] * tx;
+        py[r] = py[r - 1] * ty;
       }
-      double hx = 1.0, hy = 1.0;
+      T hx = hxT, hy = hyT;
+      wx[0] = wy[0] = T(0.5);
 #pragma unroll
-      for (int m = 0; m <= LMAX; ++m) {
-        wx[m] = (T)(m == 0 ? 1.0 : m * (m + 1) * hx);
-        wy[m] = (T)(m == 0 ? 1.0 : m * (m + 1) * hy);
-        hx *= a.hx;
-        hy *= a.hy;
+      for (int m = 1; m <= LMAX; ++m) {
+        wx[m] = T(0.5 * m * (m + 1)) * hx;
+        wy[m] = T(0.5 * m * (m + 1)) * hy;
+        hx *= hxT;
+        hy *= hyT;
       }
     }
     {
@@ -267,6 +560,8 @@ struct Stage2D {
       // outflow: columns and rows outside the mesh are ghost cells holding the constant state equal
       // to the adjacent interior cell's average (stage input for the fluxes, u~ for the jumps)
       const bool gcol = !perx && (x < 0 || x >= nx);
+      const int xw = strip * STRIP_OUT - 2;                     // column of lane 0
+      const bool edge_strip = !perx && (xw < 0 || xw + 31 >= nx);
       const bool out_lane = lane >= 2 && lane < 2 + STRIP_OUT && x >= 0 && x < nx;
       const int yb = chunk * a.H;
       const int ye = min(yb + a.H, ny);
@@ -295,139 +590,124 @@ struct Stage2D {
         }
 
         // ---- horizontal face between rows t-1 and t (once per column) ----
-        T Fh[NQ][NV];
-        if (t >= yb - 1) {
+        // Mh[v][p] = sum_g w_g P_p(x_g) F^_v(x_g): the face's flux moments, used by both rows
+        T Mh[NV][K + 1];
+        {
+          T bot[NQ][NV], top[NQ][NV];
+          edge_traces_h(u, bot, top);
+          if (t >= yb - 1) {
+            T Fh[NQ][NV];
 #pragma unroll
-          for (int g = 0; g < NQ; ++g) {
-            T bot[NV];
-            trace_at(u, &TH.v[0], g, bot);
-            llf2d<EQ, 1>(topPrev[g], bot, Fh[g], gam, gm1, ax, ay);
-          }
-          // finalise u~ of row t-1 with its top-face term
-          if (t - 1 >= yb - 1 && t - 1 <= ye) {
-            const int s = slot_of(t - 1);
+            for (int g = 0; g < NQ; ++g) llf2d<EQ, 1>(topPrev[g], bot[g], Fh[g], gam, gm1, ax, ay);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              if constexpr (PR::MIXED) {
-                T phi = T(0);
+              T F[NQ];
 #pragma unroll
-                for (int g = 0; g < NQ; ++g) phi += (T)GR::w(g) * Fh[g][v];
-                df acc0{*slot_ptr(ws, s, v, 0, lane), *slot_ptr(ws, s, v, NM, lane)};
-                acc0 = df_add(acc0, df_mul_f(dfy, -phi));
-                *slot_ptr(ws, s, v, 0, lane) = acc0.hi;
-                *slot_ptr(ws, s, v, NM, lane) = acc0.lo;
-              }
+              for (int g = 0; g < NQ; ++g) F[g] = Fh[g][v];
+              gauss_moments<0>(F, Mh[v]);
+            }
+            // finalise u~ of row t-1 with its top-face term (P_q(+1) = 1)
+            if (t - 1 >= yb - 1 && t - 1 <= ye) {
+              const int s = slot_of(t - 1);
 #pragma unroll
-              for (int m = PR::MIXED ? 1 : 0; m < NM; ++m) {
-                T sum = T(0);
-#pragma unroll
-                for (int g = 0; g < NQ; ++g) {
-                  const double c = FYT[g * NM + m];
-                  if (c != 0.0) sum += (T)c * Fh[g][v];
+              for (int v = 0; v < NV; ++v) {
+                if constexpr (PR::MIXED) {
+                  df_acc acc0{*slot_ptr(ws, s, v, 0, lane), *slot_ptr(ws, s, v, NM, lane)};
+                  acc0.add_prod(dfy, -Mh[v][0]);
+                  const df r0 = acc0.result();
+                  *slot_ptr(ws, s, v, 0, lane) = r0.hi;
+                  *slot_ptr(ws, s, v, NM, lane) = r0.lo;
                 }
-                *slot_ptr(ws, s, v, m, lane) -= (T)(0.5 * (2 * PP[m] + 1) * (2 * QQ[m] + 1)) * c1dt * inv_hy * sum;
+                T ms[K + 1];
+#pragma unroll
+                for (int p = 0; p <= K; ++p) ms[p] = sy * Mh[v][p];
+#pragma unroll
+                for (int m = PR::MIXED ? 1 : 0; m < NM; ++m)
+                  *slot_ptr(ws, s, v, m, lane) -= (T)MINV[m] * ms[PP[m]];
               }
             }
           }
+#pragma unroll
+          for (int g = 0; g < NQ; ++g)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) topPrev[g][v] = top[g][v];
         }
 
         // ---- partial u~ of row t: bottom face, vertical faces, volume, RK combination ----
         if (t >= yb - 1 && t <= ye) {
-          T acc[NV][NM];
-          T phiR[NV], phiL[NV], phiB[NV];
+          // vertical faces: F^ at xi = +1 by this lane, the one at xi = -1 from the left lane
+          T MR[NV][K + 1], ML[NV][K + 1];
+          {
+            T tl[NQ][NV], tr[NQ][NV], FR[NQ][NV], FL[NQ][NV];
+            edge_traces_v(u, tl, tr);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            phiR[v] = phiL[v] = phiB[v] = T(0);
+            for (int g = 0; g < NQ; ++g) {
+              T nb[NV];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) {
-              T sum = T(0);
+              for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[g][v], 1);
+              llf2d<EQ, 0>(tr[g], nb, FR[g], gam, gm1, ax, ay);
 #pragma unroll
-              for (int g = 0; g < NQ; ++g) {
-                const double c = FYT[g * NM + m] * ((QQ[m] & 1) ? -1.0 : 1.0);
-                if (c != 0.0) sum += (T)c * Fh[g][v];
-              }
-              acc[v][m] = sum * inv_hy;
+              for (int v = 0; v < NV; ++v) FL[g][v] = shfl_up_t(FR[g][v], 1);
             }
-#pragma unroll
-            for (int g = 0; g < NQ; ++g) phiB[v] += (T)GR::w(g) * Fh[g][v];
-          }
-          // vertical faces, one Gauss point at a time: F^_R by this lane, F^_L from the left lane
-#pragma unroll
-          for (int g = 0; g < NQ; ++g) {
-            T tl[NV], tr[NV], nb[NV], FR[NV], FL[NV];
-            trace_at(u, &TV.v[0], g, tl);
-            trace_at(u, &TV.v[NQ * NM], g, tr);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[v], 1);
-            llf2d<EQ, 0>(tr, nb, FR, gam, gm1, ax, ay);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) FL[v] = shfl_up_t(FR[v], 1);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              phiR[v] += (T)GR::w(g) * FR[v];
-              phiL[v] += (T)GR::w(g) * FL[v];
+              T FRv[NQ], FLv[NQ];
 #pragma unroll
-              for (int m = 0; m < NM; ++m) {
-                const double c = FXT[g * NM + m];
-                if (c != 0.0)
-                  acc[v][m] -= inv_hx * (T)c * (FR[v] - ((PP[m] & 1) ? -FL[v] : FL[v]));
+              for (int g = 0; g < NQ; ++g) {
+                FRv[g] = FR[g][v];
+                FLv[g] = FL[g][v];
               }
+              gauss_moments<0>(FRv, MR[v]);
+              gauss_moments<0>(FLv, ML[v]);
             }
           }
-          // volume integral at the NQ x NQ Gauss points
+          // edge terms: acc[p,q] = sy (-1)^q Mh[p] - sx (MR[q] - (-1)^p ML[q])
+          T acc[NV][NM];
 #pragma unroll
-          for (int qa = 0; qa < NQ; ++qa)
+          for (int v = 0; v < NV; ++v) {
+            T mh[K + 1], dq[K + 1], sq[K + 1];
 #pragma unroll
-            for (int qb = 0; qb < NQ; ++qb) {
-              const int base = (qa * NQ + qb) * NM;
-              T uq[NV], fx[NV], fy[NV];
-#pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                T sacc = T(0);
-#pragma unroll
-                for (int m = 0; m < NM; ++m) {
-                  const double c = VE[base + m];
-                  if (c != 0.0) sacc += u[v][m] * (T)c;
-                }
-                uq[v] = sacc;
-              }
-              flux2d_xy<EQ>(uq, fx, fy, gm1, ax, ay);
-#pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                const T fxs = fx[v] * inv_hx, fys = fy[v] * inv_hy;
-#pragma unroll
-                for (int m = 0; m < NM; ++m) {
-                  const double cx = VX[base + m], cy = VY[base + m];
-                  if (cx != 0.0) acc[v][m] += fxs * (T)cx;
-                  if (cy != 0.0) acc[v][m] += fys * (T)cy;
-                }
-              }
+            for (int i = 0; i <= K; ++i) {
+              mh[i] = sy * Mh[v][i];
+              dq[i] = sx * (ML[v][i] - MR[v][i]);
+              sq[i] = -sx * (ML[v][i] + MR[v][i]);
             }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+              const T hb = (QQ[m] & 1) ? -mh[PP[m]] : mh[PP[m]];
+              acc[v][m] = hb + ((PP[m] & 1) ? sq[QQ[m]] : dq[QQ[m]]);
+            }
+          }
+          volume(u, acc, sx, sy, gm1, ax, ay);
+
           const int s = slot_of(t);
           T un_[NV][NM], unlo[NV];
           if (a.stage > 0) ST::load(a.un, a.ncell, cell, un_, unlo);
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if constexpr (PR::MIXED) {
-              // cell average in double-float from the edge integrals, each computed once per edge:
-              // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B - Phi_T)
-              df m0{u[v][0], lo0[v]};
+              // cell average in double-float from the edge integrals, each formed once per edge:
+              // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B [- Phi_T at the next row])
+              df_acc m0{u[v][0], lo0[v]};
               if (a.stage > 0) {
-                const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
-                m0 = df_add(m0, df_mul(dfc0, d));
+                df_acc d{un_[v][0], unlo[v]};
+                d.add(df{-u[v][0], -lo0[v]});
+                const df dd = d.result();
+                m0.add(df_mul(dfc0, dd));
               }
-              m0 = df_add(m0, df_mul_f(dfx, phiL[v]));
-              m0 = df_add(m0, df_mul_f(dfx, -phiR[v]));
-              m0 = df_add(m0, df_mul_f(dfy, phiB[v]));
-              *slot_ptr(ws, s, v, 0, lane) = m0.hi;
-              *slot_ptr(ws, s, v, NM, lane) = m0.lo;
+              m0.add_prod(dfx, ML[v][0]);
+              m0.add_prod(dfx, -MR[v][0]);
+              m0.add_prod(dfy, Mh[v][0]);
+              const df r0 = m0.result();
+              *slot_ptr(ws, s, v, 0, lane) = r0.hi;
+              *slot_ptr(ws, s, v, NM, lane) = r0.lo;
             }
 #pragma unroll
             for (int m = PR::MIXED ? 1 : 0; m < NM; ++m) {
-              const T R = (T)(0.5 * (2 * PP[m] + 1) * (2 * QQ[m] + 1)) * acc[v][m];
               // u + c0 (u^n - u) + c1 dt R  (= c0 u^n + c1 (u + dt R) with c0 + c1 = 1 kept exact)
-              T val = u[v][m] + c1dt * R;
+              T val = u[v][m];
               if (a.stage > 0) val += c0 * (un_[v][m] - u[v][m]);
+              val += (T)MINV[m] * acc[v][m];
               *slot_ptr(ws, s, v, m, lane) = val;
             }
           }
@@ -474,7 +754,7 @@ struct Stage2D {
 #pragma unroll
               for (int m = 1; m < NM; ++m) u2[m] = T(0);
             }
-            {
+            if (edge_strip) {                                   // warp-uniform: a strip at an outflow side
               const T v_r = shfl_down_t(uv[0], 1), v_l = shfl_up_t(uv[0], 1);
               const T w_r = shfl_down_t(u2[0], 1), w_l = shfl_up_t(u2[0], 1);
               if (gcol) {
@@ -484,31 +764,35 @@ struct Stage2D {
                 for (int m = 1; m < NM; ++m) uv[m] = u2[m] = T(0);
               }
             }
+            // eta-derivatives at the horizontal edges: row t-1 at eta = -1 and +1, row t-2 at +1
+            T Hb[K + 1][K + 1], Ht[K + 1][K + 1], H2[K + 1][K + 1];
+            eta_ends<true>(uv, Hb, Ht);
+            eta_ends<false>(u2, H2, H2);
             T svr[LMAX + 1], sh[LMAX + 1];
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) svr[l] = sh[l] = T(0);
-#pragma unroll
-            for (int aa = 0; aa < NA; ++aa) {
-              // corner values of d^alpha u~: c00 = (xi,eta) = (-1,-1), c01 = (-1,+1), c10, c11
-              T c00 = T(0), c01 = T(0), c10 = T(0), c11 = T(0), t01 = T(0), t11 = T(0);
-#pragma unroll
-              for (int m = 0; m < NM; ++m) {
-                const double k00 = CT[(0 * NA + aa) * NM + m], k01 = CT[(1 * NA + aa) * NM + m];
-                const double k10 = CT[(2 * NA + aa) * NM + m], k11 = CT[(3 * NA + aa) * NM + m];
-                if (k00 != 0.0) c00 += uv[m] * (T)k00;
-                if (k01 != 0.0) { c01 += uv[m] * (T)k01; t01 += u2[m] * (T)k01; }
-                if (k10 != 0.0) c10 += uv[m] * (T)k10;
-                if (k11 != 0.0) { c11 += uv[m] * (T)k11; t11 += u2[m] * (T)k11; }
-              }
-              const T f = px[A1[aa]] * py[A2[aa]];
-              c00 *= f; c01 *= f; c10 *= f; c11 *= f; t01 *= f; t11 *= f;
-              const int l = A1[aa] + A2[aa];
-              if (need_v) {
-                const T n0 = shfl_down_t(c00, 1), n1 = shfl_down_t(c01, 1);
-                svr[l] += T(0.5) * (fabs(c10 - n0) + fabs(c11 - n1));
-              }
-              sh[l] += T(0.5) * (fabs(c00 - t01) + fabs(c10 - t11));
-            }
+            sfor<K + 1>([&](auto B2) {
+              constexpr int a2 = decltype(B2)::value;
+              sfor<K + 1>([&](auto B1) {
+                constexpr int a1 = decltype(B1)::value;
+                if constexpr (TB::alpha_ok(a1, a2)) {
+                  // corner values of d^alpha u~: c00 = (xi,eta) = (-1,-1), c01 = (-1,+1), c10, c11;
+                  // t01, t11: the top corners of row t-2
+                  T c00, c01, c10, c11, t01, t11;
+                  xi_ends<a1, a2>(Hb, c10, c00);
+                  xi_ends<a1, a2>(Ht, c11, c01);
+                  xi_ends<a1, a2>(H2, t11, t01);
+                  // physical derivatives: the same positive factor (2/hx)^a1 (2/hy)^a2 on both sides
+                  const T f = px[a1] * py[a2];
+                  constexpr int l = a1 + a2;
+                  if (need_v) {
+                    const T n0 = shfl_down_t(c00, 1), n1 = shfl_down_t(c01, 1);
+                    svr[l] += f * (fabs(c10 - n0) + fabs(c11 - n1));
+                  }
+                  sh[l] += f * (fabs(c00 - t01) + fabs(c10 - t11));
+                }
+              });
+            });
             T av = T(0), shc = T(0);
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) {
@@ -565,8 +849,6 @@ struct Stage2D {
         by2 = by1;
         invH2 = invH1;
         phys2 = phys1;
-#pragma unroll
-        for (int g = 0; g < NQ; ++g) trace_at(u, &TH.v[NQ * NM], g, topPrev[g]);
       }
     }
   }
