@@ -36,7 +36,8 @@ class _Problem(C.Structure):
                 ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
                 ("bc", C.c_int * 4), ("k", C.c_int), ("basis", C.c_int), ("eq", C.c_int),
                 ("gamma", C.c_double), ("adv", C.c_double * 2), ("filter", C.c_int),
-                ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int), ("positivity", C.c_int)]
+                ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int), ("positivity", C.c_int),
+                ("hybrid", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -59,6 +60,7 @@ class Problem:
     nq: int = 0
     filter_dt_mode: int = 0
     positivity: int = 0
+    hybrid: int = 0
 
     def c(self) -> _Problem:
         s = _Problem()
@@ -120,6 +122,7 @@ def lib():
             "orc_dt": (D, [P, dp, D, D]), "orc_residual": (None, [P, dp, dp]),
             "orc_filter": (None, [P, dp, D, dp]), "orc_filter_sigma": (None, [P, dp, dp]),
             "orc_positivity": (None, [P, dp]),
+            "orc_jump_indicator": (None, [P, dp, dp]), "orc_hybrid": (None, [P, dp, D, dp]),
             "orc_rk_stage": (None, [P, I, dp, dp, D, dp]), "orc_step": (I, [P, dp, D]),
             "orc_advance": (I, [P, dp, D, D, C.c_long, dp, C.POINTER(C.c_long)]),
             "orc_check_physical": (I, [P, dp]), "orc_mass": (None, [P, dp, dp]),
@@ -239,6 +242,24 @@ def positivity(p: Problem, u) -> np.ndarray:
     pc = p.c()
     lib().orc_positivity(C.byref(pc), _dp(u))
     return u
+
+
+def jump_indicator(p: Problem, u) -> np.ndarray:
+    """eta_j of Algorithm 1 per cell (first conservative variable)."""
+    u = _arr(u)
+    eta = np.zeros(p.ncell)
+    pc = p.c()
+    lib().orc_jump_indicator(C.byref(pc), _dp(u), _dp(eta))
+    return eta
+
+
+def hybrid(p: Problem, u, dt_: float) -> np.ndarray:
+    """u^hyd of Algorithm 1 from a DG solution u: troubled cells blended with the jump filter."""
+    u = _arr(u)
+    out = np.zeros_like(u)
+    pc = p.c()
+    lib().orc_hybrid(C.byref(pc), _dp(u), float(dt_), _dp(out))
+    return out
 
 
 def filter_sigma(p: Problem, u) -> np.ndarray:

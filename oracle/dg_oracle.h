@@ -63,6 +63,7 @@ typedef struct {
   int filter_dt_mode;      /* 0: exp(-sigma*dt) with the full step dt after every stage;
                               1: the stage's own effective step (dt, dt/4, 2dt/3) */
   int positivity;          /* Euler: 1 = Zhang-Shu positivity-preserving limiter after the filter */
+  int hybrid;              /* 1 = hybrid limiter of Algorithm 1 (jump filter as the low-order part) */
 } orc_problem;
 
 /* ---- basis (orc_basis.c) ---- */
@@ -88,6 +89,8 @@ double orc_dt(const orc_problem* p, const double* u, double t, double T);
 void   orc_residual(const orc_problem* p, const double* u, double* R);
 void   orc_filter(const orc_problem* p, const double* u, double dt, double* out);
 void   orc_positivity(const orc_problem* p, double* u);            /* Zhang-Shu limiter, in place */
+void   orc_jump_indicator(const orc_problem* p, const double* u, double* eta); /* Algorithm 1 eta_j */
+void   orc_hybrid(const orc_problem* p, const double* u, double dt, double* out);  /* Algorithm 1 */
 void   orc_filter_sigma(const orc_problem* p, const double* u, double* sigma); /* sigma^l per cell, l=0..lmax */
 void   orc_rk_stage(const orc_problem* p, int s, const double* un, const double* us, double dt, double* out);
 int    orc_step(const orc_problem* p, double* u, double dt);  /* one SSP-RK3 step in place; 0 = ok */

@@ -396,6 +396,77 @@ void orc_filter(const orc_problem* p, const double* u, double dt, double* out) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Hybrid limiter of Algorithm 1 (Section 2.4): the jump indicator eta_j flags troubled cells, on  */
+/* which the DG solution is blended with its jump-filtered version u^lim by the weight            */
+/* omega_j = (max eta - eta_j) / (max eta - 1); elsewhere the DG solution is kept unfiltered.      */
+/* The indicator is taken on the first conservative variable (density for Euler); 1D:             */
+/* eta_j = (|[u]_{j-1/2}| + |[u]_{j+1/2}|) / (2 h); 2D: the same per direction with each edge's    */
+/* jump averaged over its two corners, eta = J^V / (2 h_x) + J^H / (2 h_y), so that y-invariant   */
+/* data give the 1D value. Outflow ghosts hold the cell average, as for the filter.              */
+/* ------------------------------------------------------------------------------------------ */
+static double eta_cell(const orc_problem* p, const ctx_t* c, const double* u, long cell) {
+  if (p->dim == 1) {
+    long il = neighbour(p, (int)cell, 0, 0, 0), ir = neighbour(p, (int)cell, 0, 0, 1);
+    const double ghost = U(u, 0, 0, cell);
+    double nl = il >= 0 ? end_deriv_1d(c, u, 0, il, 1, 0) : ghost;
+    double nr = ir >= 0 ? end_deriv_1d(c, u, 0, ir, 0, 0) : ghost;
+    double jl = fabs(end_deriv_1d(c, u, 0, cell, 0, 0) - nl);
+    double jr = fabs(nr - end_deriv_1d(c, u, 0, cell, 1, 0));
+    return (jl + jr) / (2.0 * c->hx);
+  }
+  const int nx = p->nx;
+  int i = (int)(cell % nx), j = (int)(cell / nx);
+  long nl = neighbour(p, i, j, 0, 0), nr = neighbour(p, i, j, 0, 1);
+  long nb = neighbour(p, i, j, 1, 0), nt = neighbour(p, i, j, 1, 1);
+  const double ghost = U(u, 0, 0, cell);
+  double jv = 0.0, jh = 0.0;
+  for (int cy = 0; cy <= 1; ++cy) {
+    double gl = nl >= 0 ? corner_deriv_2d(c, u, 0, nl, 1, cy, 0, 0) : ghost;
+    double gr = nr >= 0 ? corner_deriv_2d(c, u, 0, nr, 0, cy, 0, 0) : ghost;
+    jv += 0.5 * fabs(corner_deriv_2d(c, u, 0, cell, 0, cy, 0, 0) - gl);
+    jv += 0.5 * fabs(gr - corner_deriv_2d(c, u, 0, cell, 1, cy, 0, 0));
+  }
+  for (int cx = 0; cx <= 1; ++cx) {
+    double gb = nb >= 0 ? corner_deriv_2d(c, u, 0, nb, cx, 1, 0, 0) : ghost;
+    double gt = nt >= 0 ? corner_deriv_2d(c, u, 0, nt, cx, 0, 0, 0) : ghost;
+    jh += 0.5 * fabs(corner_deriv_2d(c, u, 0, cell, cx, 0, 0, 0) - gb);
+    jh += 0.5 * fabs(gt - corner_deriv_2d(c, u, 0, cell, cx, 1, 0, 0));
+  }
+  return jv / (2.0 * c->hx) + jh / (2.0 * c->hy);
+}
+
+void orc_jump_indicator(const orc_problem* p, const double* u, double* eta) {
+  ctx_t c;
+  make_ctx(p, &c);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+  for (long cell = 0; cell < c.ncell; ++cell) eta[cell] = eta_cell(p, &c, u, cell);
+}
+
+/* u^hyd of Algorithm 1 from the DG solution u (after the Runge-Kutta combination of a stage). */
+void orc_hybrid(const orc_problem* p, const double* u, double dt, double* out) {
+  ctx_t cc;
+  make_ctx(p, &cc);
+  const ctx_t* c = &cc;
+  long n = orc_state_size(p);
+  double* lim = (double*)malloc(sizeof(double) * n);
+  double* eta = (double*)malloc(sizeof(double) * c->ncell);
+  orc_filter(p, u, dt, lim);                           /* u^lim: the jump filter of u^DG */
+  orc_jump_indicator(p, u, eta);
+  double emax = 0.0;
+  for (long cell = 0; cell < c->ncell; ++cell)
+    if (eta[cell] > emax || isnan(eta[cell])) emax = eta[cell];
+  for (long cell = 0; cell < c->ncell; ++cell) {
+    const int troubled = eta[cell] > 1.0;
+    const double w = troubled ? (emax - eta[cell]) / (emax - 1.0) : 1.0;
+    for (int v = 0; v < c->nv; ++v)
+      for (int m = 0; m < c->nm; ++m)
+        U(out, v, m, cell) = troubled ? w * U(u, v, m, cell) + (1.0 - w) * U(lim, v, m, cell) : U(u, v, m, cell);
+  }
+  free(lim);
+  free(eta);
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Positivity-preserving limiter of Zhang and Shu (J. Comput. Phys. 229, 2010), applied after the */
 /* jump filter when the problem asks for it (the paper does so in Section 3.2).                   */
 /* Checked at every point where the scheme evaluates the cell polynomial: the volume Gauss points */
@@ -491,7 +562,8 @@ void orc_rk_stage(const orc_problem* p, int s, const double* un, const double* u
   }
   if (p->filter) {
     double fdt = p->filter_dt_mode == 1 ? dt * SO_D[s][s] : dt;
-    orc_filter(p, tmp, fdt, out);
+    if (p->hybrid) orc_hybrid(p, tmp, fdt, out);   /* Algorithm 1 after every stage */
+    else orc_filter(p, tmp, fdt, out);
   } else {
     memcpy(out, tmp, sizeof(double) * n);
   }
