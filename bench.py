@@ -243,11 +243,11 @@ def run_served(N, stream, rate, n_req, budget):
     return out
 
 
-def make_solver(N, precision, nx, seed, stream, tile=(0, 0)):
+def make_solver(N, precision, nx, seed, stream, tile=(0, 0), hybrid=0):
     from paper_2407_19169_gb300 import inputs as I
     s = N.Solver(dim=2, nx=nx, ny=nx, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(N.BC_OUTFLOW,) * 4, k=2,
                  eq=N.EQ_EULER, filter=1, cfl=0.1, gamma=1.4, precision=precision, stream=stream,
-                 tile_rows=tile[0], tile_warps=tile[1])
+                 tile_rows=tile[0], tile_warps=tile[1], hybrid=hybrid)
     s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(seed))
     return s
 
@@ -346,6 +346,8 @@ def main():
     ap.add_argument("--skip-tune", action="store_true")
     ap.add_argument("--tile-rows", type=int, default=0, help="force the 2D tile rows (skips tuning)")
     ap.add_argument("--tile-warps", type=int, default=0, help="force the warps per block")
+    ap.add_argument("--skip-hybrid", action="store_true")
+    ap.add_argument("--hybrid-steps", type=int, default=100)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=200)
@@ -415,6 +417,20 @@ def main():
         s64.close()
         del s64
 
+    # ---- the hybrid limiter of Algorithm 1 on the same problem (stage kernel + blend kernel) ----
+    hybrid = None
+    if not args.skip_hybrid:
+        sh_ = make_solver(N, N.PREC_FP32_MIXED, nx, seed, sh, tile, hybrid=1)
+        sh_.advance_steps(args.warmup)
+        torch.cuda.synchronize()
+        msh, launchesh = time_steps(torch, sh_, args.hybrid_steps, stream, barrier)
+        hybrid = {"value": 3.0 * ndof * args.hybrid_steps / (msh * 1e-3), "unit": UNIT, "steps": args.hybrid_steps,
+                  "ms_per_step": msh / args.hybrid_steps, "gpu_launches": launchesh, "dtype": "f32+df64",
+                  "note": "Algorithm 1 after every stage: eta and filter factors from the stage kernel, "
+                          "max eta, then the troubled cells blended by a second kernel"}
+        sh_.close()
+        del sh_
+
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if not args.skip_e2e:
@@ -469,6 +485,7 @@ def main():
         "fp64": fp64,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": e2e,
+        "hybrid": hybrid,
         "batched": batched,
         "served": served,
     }

@@ -94,7 +94,13 @@ typedef struct {
  *   positivity Euler only: 1 = the positivity-preserving limiter of Zhang and Shu after the filter in
  *             every stage (the paper applies it this way in Section 3.2), 0 = off (default): density
  *             and pressure are kept >= min(1e-10, rho_bar, p_bar) at the volume and edge Gauss points
- *             by scaling the modes l >= 1; cell averages are untouched */
+ *             by scaling the modes l >= 1; cell averages are untouched
+ *   hybrid    1 = the hybrid limiter of Algorithm 1 (Section 2.4) after every stage instead of the
+ *             plain filter: cells whose jump indicator eta_j = ||[rho]||_{dK_j} / (2h) exceeds 1 are
+ *             blended with their jump-filtered version by omega_j = (max eta - eta_j)/(max eta - 1),
+ *             the others keep the unfiltered DG solution. Needs enabled = 1 and positivity = 0
+ *             (DG_ERR_UNSUPPORTED otherwise); not available in dg_batch_run or dg_step_noalloc.
+ *             0 = off (default) */
 typedef struct {
   int enabled;
   double cfl;
@@ -108,6 +114,7 @@ typedef struct {
   int tile_rows;
   int tile_warps;
   int positivity;
+  int hybrid;
 } dg_filter_params;
 
 typedef struct dg_solver dg_solver; /* opaque, library-owned */

@@ -39,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("enabled", C.c_int), ("cfl", C.c_double), ("gamma", C.c_double),
                 ("adv_speed", C.c_double * 2), ("basis", C.c_int), ("nq", C.c_int), ("precision", C.c_int),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("tile_rows", C.c_int),
-                ("tile_warps", C.c_int), ("positivity", C.c_int)]
+                ("tile_warps", C.c_int), ("positivity", C.c_int),
+                ("hybrid", C.c_int)]
 
 
 class DGError(RuntimeError):
@@ -121,7 +122,7 @@ class Solver:
     def __init__(self, dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(BC_PERIODIC,) * 4, k=2,
                  eq=EQ_BURGERS, filter=1, cfl=0.1, gamma=1.4, adv=(1.0, 0.0), basis=BASIS_Q,
                  precision=PREC_FP64, stream=None, tile_rows=0, workspace=None, tile_warps=0,
-                 positivity=0):
+                 positivity=0, hybrid=0):
         L = load()
         self.mesh = Mesh(dim, nx, ny, x0, x1, y0, y1, (C.c_int * 4)(*bc))
         self.params = Params()
@@ -135,6 +136,7 @@ class Solver:
         self.params.tile_rows = tile_rows
         self.params.tile_warps = tile_warps
         self.params.positivity = positivity
+        self.params.hybrid = hybrid
         self._workspace = workspace  # keep a caller tensor alive
         if workspace is not None:
             self.params.workspace = workspace.data_ptr()
@@ -150,13 +152,14 @@ class Solver:
 
     @staticmethod
     def workspace_size(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(BC_PERIODIC,) * 4, k=2,
-                       eq=EQ_BURGERS, basis=BASIS_Q, precision=PREC_FP64) -> int:
+                       eq=EQ_BURGERS, basis=BASIS_Q, precision=PREC_FP64, hybrid=0) -> int:
         L = load()
         mesh = Mesh(dim, nx, ny, x0, x1, y0, y1, (C.c_int * 4)(*bc))
         p = Params()
         check(L.dg_params_default(C.byref(p)), "dg_params_default")
         p.basis = basis
         p.precision = precision
+        p.hybrid = hybrid
         n = C.c_size_t()
         check(L.dg_workspace_size(C.byref(mesh), k, eq, C.byref(p), C.byref(n)), "dg_workspace_size")
         return n.value

@@ -267,6 +267,57 @@ __global__ void from_storage_kernel(const AuxGeom g, const void* st, double* can
   }
 }
 
+int hybrid_lmax(const AuxGeom& g) { return g.dim == 1 ? g.k : (g.basis == 0 ? 2 * g.k : g.k); }
+
+// Algorithm 1, after a stage kernel that stored the DG solution: on each listed troubled cell,
+// u^hyd = omega u^DG + (1 - omega) u^lim with u^lim's mode of total degree l equal to
+// exp(-sigma^l dt) u^DG's, i.e. each higher mode scaled by omega + (1 - omega) exp(-sigma^l dt),
+// omega = (max eta - eta) / (max eta - 1). Cell averages are untouched. The last block to finish
+// clears the count and the maximum for the next stage.
+__global__ void hybrid_blend_kernel(const AuxGeom g, void* st, const HybridOut h) {
+  volatile HybridScalars* vs = h.sc;
+  const unsigned n = vs->count;
+  const double emax = __longlong_as_double((long long)vs->max_bits);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long c = h.list[i];
+    if (g.prec == PREC_F64) {
+      const double e = ((const double*)h.eta)[c];
+      const double w = (emax - e) / (emax - 1.0);
+      double* b = (double*)st;
+      for (int m = 1; m < g.nm; ++m) {
+        const int l = g.mp[m] + g.mq[m];
+        const double f = w + (1.0 - w) * ((const double*)h.fac)[(long long)(l - 1) * g.ncell + c];
+        for (int v = 0; v < g.nv; ++v) b[((long long)v * g.nm + m) * g.ncell + c] *= f;
+      }
+    } else {
+      const float e = ((const float*)h.eta)[c];
+      const float w = (float)((emax - (double)e) / (emax - 1.0));
+      float* bh = (float*)((char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+      for (int m = 1; m < g.nm; ++m) {
+        const int l = g.mp[m] + g.mq[m];
+        const float f = w + (1.0f - w) * ((const float*)h.fac)[(long long)(l - 1) * g.ncell + c];
+        for (int v = 0; v < g.nv; ++v) bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c] *= f;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&h.sc->blocks, 1u);
+    if (prev == gridDim.x - 1) {
+      vs->count = 0u;
+      vs->max_bits = 0ull;
+      vs->blocks = 0u;
+      __threadfence();
+    }
+  }
+}
+
+cudaError_t launch_hybrid_blend(const AuxGeom& g, void* state, const HybridOut& h, cudaStream_t s) {
+  hybrid_blend_kernel<<<304, 256, 0, s>>>(g, state, h);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_storage(const AuxGeom& g, const double* canon, void* state, cudaStream_t s) {
   to_storage_kernel<<<1216, 256, 0, s>>>(g, canon, state);
   return cudaGetLastError();

@@ -88,6 +88,7 @@ static dg_status validate(const dg_mesh* m, int k, int eq, const dg_filter_param
   if (p->precision != DG_PREC_FP64 && p->precision != DG_PREC_FP32_MIXED) return DG_ERR_ARG;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0)) return DG_ERR_ARG;
   if ((long long)m->nx * (m->dim == 2 ? m->ny : 1) > (1LL << 31)) return DG_ERR_UNSUPPORTED;
+  if (p->hybrid && (!p->enabled || p->positivity)) return DG_ERR_UNSUPPORTED;
   return DG_OK;
 }
 
@@ -113,6 +114,7 @@ static void fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filt
   g.ax = p->adv_speed[0];
   g.ay = p->adv_speed[1];
   g.pp = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
+  g.hyb = p->hybrid ? 1 : 0;
   int idx = 0;
   if (m->dim == 1) {
     for (int l = 0; l <= k; ++l) { g.mp[l] = l; g.mq[l] = 0; }
@@ -129,7 +131,8 @@ static void fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filt
 
 // Layout of the single device allocation.
 struct Layout {
-  size_t off_buf[3], off_canon, off_part, off_mass, off_sc, total;
+  size_t off_buf[3], off_canon, off_part, off_mass, off_sc, off_hy_eta, off_hy_fac, off_hy_list, off_hy_sc,
+      total;
 };
 static Layout layout_of(const AuxGeom& g) {
   Layout L;
@@ -143,6 +146,18 @@ static Layout layout_of(const AuxGeom& g) {
   o += 256;
   L.off_sc = o;
   o += align256(sizeof(DevScalars));
+  L.off_hy_eta = L.off_hy_fac = L.off_hy_list = L.off_hy_sc = 0;
+  if (g.hyb) {
+    const size_t ts = g.prec == PREC_F64 ? sizeof(double) : sizeof(float);
+    L.off_hy_eta = o;
+    o += align256(ts * (size_t)g.ncell);
+    L.off_hy_fac = o;
+    o += align256(ts * (size_t)hybrid_lmax(g) * g.ncell);
+    L.off_hy_list = o;
+    o += align256(sizeof(int) * (size_t)g.ncell);
+    L.off_hy_sc = o;
+    o += align256(sizeof(HybridScalars));
+  }
   L.total = o;
   return L;
 }
@@ -229,6 +244,7 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
   s->prec = params->precision == DG_PREC_FP64 ? PREC_F64 : PREC_F32M;
   s->filter_on = params->enabled ? 1 : 0;
   s->positivity = (params->positivity && equation == DG_EQ_EULER) ? 1 : 0;
+  s->hybrid = params->hybrid ? 1 : 0;
   s->cfl = params->cfl;
   s->gamma = params->gamma;
   s->ax = params->adv_speed[0];
@@ -276,6 +292,13 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
   s->partials = (double*)(base + Lo.off_part);
   s->dmass = (double*)(base + Lo.off_mass);
   s->sc = (DevScalars*)(base + Lo.off_sc);
+  s->hy = HybridOut{};
+  if (s->hybrid) {
+    s->hy.eta = base + Lo.off_hy_eta;
+    s->hy.fac = base + Lo.off_hy_fac;
+    s->hy.list = (int*)(base + Lo.off_hy_list);
+    s->hy.sc = (HybridScalars*)(base + Lo.off_hy_sc);
+  }
   ce = cudaMallocHost(&s->h_sc, sizeof(DevScalars));
   if (ce != cudaSuccess) {
     s->h_sc = nullptr;
@@ -470,6 +493,8 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.cfl = s->cfl;
       a.nwarps = s->nwarps1d;
       a.positivity = s->positivity;
+      a.hybrid = s->hybrid;
+      a.hyb = s->hy;
       a.sc = s->sc;
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     } else {
@@ -496,11 +521,19 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.nstrips = s->nstrips;
       a.nchunks = s->nchunks;
       a.positivity = s->positivity;
+      a.hybrid = s->hybrid;
+      a.hyb = s->hy;
       a.sc = s->sc;
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     }
     if (e != cudaSuccess) return e;
     s->launches += 1;
+    if (s->hybrid) {
+      // Algorithm 1: blend the troubled cells once max eta of this stage is known
+      e = launch_hybrid_blend(s->geom, dsts[st], s->hy, s->stream);
+      if (e != cudaSuccess) return e;
+      s->launches += 1;
+    }
   }
   return cudaSuccess;
 }
@@ -513,6 +546,7 @@ static dg_status ensure_pair_graph(dg_solver* s) {
   cudaError_t e1 = launch_step(s, 0);
   cudaError_t e2 = e1 == cudaSuccess ? launch_step(s, 1) : e1;
   cudaError_t e3 = cudaStreamEndCapture(s->stream, &g);
+  s->pair_launches = s->launches - saved;
   s->launches = saved;
   if (e2 != cudaSuccess) return cuda_fail(e2, "capture step pair");
   if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamEndCapture");
@@ -549,7 +583,7 @@ static dg_status enqueue_steps(dg_solver* s, long long n) {
   }
   while (left >= 2) {
     CK(cudaGraphLaunch(s->pair_exec, s->stream));
-    s->launches += 6;
+    s->launches += s->pair_launches;
     s->h_step += 2;
     left -= 2;
   }

@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
     a.nstrips = I.nstrips;
     a.nchunks = I.nchunks;
     a.positivity = I.positivity;
+    a.hybrid = 0;
+    a.hyb = HybridOut{};
     a.sc = I.sc;
     const long long local = w - I.item0;
     double r = 0.0;
@@ -136,6 +138,8 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
     a.cfl = I.cfl;
     a.nwarps = I.nstrips;
     a.positivity = I.positivity;
+    a.hybrid = 0;
+    a.hyb = HybridOut{};
     a.sc = I.sc;
     double r = 0.0;
     T rt = T(0);
@@ -228,7 +232,7 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
   for (int i = 0; i < n; ++i) {
     const dg_solver* s = solvers[i];
     if (!s) return DG_ERR_ARG;
-    if (s->eq != DG_EQ_EULER || s->prec != PREC_F32M || (s->dim == 2 && s->basis != DG_BASIS_Q))
+    if (s->eq != DG_EQ_EULER || s->prec != PREC_F32M || (s->dim == 2 && s->basis != DG_BASIS_Q) || s->hybrid)
       return DG_ERR_UNSUPPORTED;
   }
   if (cudaGetDevice(&dev0) != cudaSuccess) return DG_ERR_CUDA;

@@ -35,6 +35,22 @@ struct DevScalars {
   unsigned int is_last;           // current step is clipped to land on T_end
 };
 
+// Hybrid limiter (Algorithm 1) of one solver: the stage kernel stores the unfiltered DG solution
+// and, per output cell, the jump indicator eta and the filter factors exp(-sigma^l dt), l >= 1; it
+// appends the troubled cells (eta > 1) to `list` and maxes eta into `max_bits`. The blend kernel
+// then rescales the higher modes of the listed cells and clears the scalars for the next stage.
+struct HybridScalars {
+  unsigned long long max_bits;    // max eta over the stage (bits of a non-negative double)
+  unsigned int count;             // troubled cells listed
+  unsigned int blocks;            // last-block counter of the blend kernel
+};
+struct HybridOut {
+  void* eta;                      // [ncell], stage arithmetic type
+  void* fac;                      // [LMAX][ncell], factor of total degree l = 1..LMAX
+  int* list;                      // [ncell] troubled cells
+  HybridScalars* sc;
+};
+
 __host__ __device__ constexpr double cfact(int n) {
   double r = 1.0;
   for (int i = 2; i <= n; ++i) r *= i;

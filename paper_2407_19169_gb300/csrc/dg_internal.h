@@ -29,6 +29,7 @@ struct AuxGeom {
   double x0, y0, hx, hy, gamma, ax, ay;
   int mp[16], mq[16];  // (p, q) of each mode
   int pp;              // Euler with the positivity limiter: the CFL rate also takes the limiter's points
+  int hyb;             // hybrid limiter (Algorithm 1) scratch in the workspace
 };
 
 cudaError_t aux_init_tables();  // copy Gauss rules to constant memory of the current device
@@ -39,6 +40,10 @@ cudaError_t launch_to_storage(const AuxGeom& g, const double* canon, void* state
 cudaError_t launch_from_storage(const AuxGeom& g, const void* state, double* canon, cudaStream_t s);
 cudaError_t launch_mass(const AuxGeom& g, const void* state, double* partials, double* out, cudaStream_t s);
 size_t state_bytes(const AuxGeom& g);
+// Hybrid limiter: rescale the higher modes of the listed troubled cells of `state` by
+// omega + (1 - omega) exp(-sigma^l dt), then clear the stage's scalars.
+cudaError_t launch_hybrid_blend(const AuxGeom& g, void* state, const HybridOut& h, cudaStream_t s);
+int hybrid_lmax(const AuxGeom& g);   // highest total degree l of a mode
 constexpr int MASS_BLOCKS = 256;
 
 }  // namespace dgk

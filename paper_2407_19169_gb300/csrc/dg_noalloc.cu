@@ -66,7 +66,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
   if (m->bc[0] != m->bc[1] || (m->dim == 2 && m->bc[2] != m->bc[3])) return DG_ERR_ARG;
   if (eq < DG_EQ_ADVECTION || eq > DG_EQ_EULER) return DG_ERR_ARG;
   if (k < 1 || k > 3 || (p->nq != 0 && p->nq != k + 1)) return DG_ERR_UNSUPPORTED;
-  if (p->precision != DG_PREC_FP64) return DG_ERR_UNSUPPORTED;
+  if (p->precision != DG_PREC_FP64 || p->hybrid) return DG_ERR_UNSUPPORTED;
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0)) return DG_ERR_ARG;
   const int dim = m->dim;
   const int basis = dim == 2 ? p->basis : DG_BASIS_Q;
@@ -140,6 +140,8 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.cfl = p->cfl;
       a.nwarps = nwarps;
       a.positivity = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
+      a.hybrid = 0;
+      a.hyb = HybridOut{};
       a.sc = sc;
       if (L.launch(&a, (unsigned)((nwarps + 3) / 4), 128, 256, st) != cudaSuccess) return DG_ERR_CUDA;
     }
@@ -182,6 +184,8 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.nstrips = nstrips;
       a.nchunks = nchunks;
       a.positivity = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
+      a.hybrid = 0;
+      a.hyb = HybridOut{};
       a.sc = sc;
       if (L.launch(&a, (unsigned)((nw + wpb - 1) / wpb), 32 * wpb, smem, st) != cudaSuccess) return DG_ERR_CUDA;
     }

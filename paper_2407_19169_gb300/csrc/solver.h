@@ -7,7 +7,7 @@
 
 struct dg_solver {
   dg_mesh mesh;
-  int k, eq, dim, basis, prec, filter_on, H, warps_per_block, positivity;
+  int k, eq, dim, basis, prec, filter_on, H, warps_per_block, positivity, hybrid;
   double cfl, gamma, ax, ay;
   dgk::AuxGeom geom;
   size_t ndof, sbytes;
@@ -21,6 +21,7 @@ struct dg_solver {
   double* partials;     // mass partial sums
   double* dmass;        // mass result
   dgk::DevScalars* sc;
+  dgk::HybridOut hy;    // hybrid limiter scratch (null pointers when off)
   dgk::DevScalars* h_sc;  // pinned mirror
   long long h_step;     // host's record of the device step count (buffer parity)
   dgk::StageLauncher L;
@@ -29,6 +30,7 @@ struct dg_solver {
   int nstrips, nchunks, nwarps1d;
   cudaGraphExec_t pair_exec;
   bool pair_ready;
+  long long pair_launches;  // kernel nodes in the step-pair graph
   long long launches;
 };
 

@@ -32,6 +32,8 @@ struct Stage1DArgs {
   double gamma, ax, cfl;
   int nwarps;
   int positivity;    // Euler: Zhang-Shu limiter after the filter
+  int hybrid;        // hybrid limiter (Algorithm 1): store u^DG, eta and the filter factors
+  HybridOut hyb;
   DevScalars* sc;
 };
 
@@ -59,6 +61,7 @@ struct Stage1D {
     // double-float coefficients of the cell-average update (once per item, off the cell path)
     const df dcf = df_from_double(a.c1 * dtd / a.h);
     const df dc0 = df_from_double(a.c0);
+    T my_eta = T(0);
     {
       const int x = (int)strip * STRIP_OUT - 2 + lane;
       const bool per = a.bc == BC_PERIODIC;
@@ -197,7 +200,7 @@ struct Stage1D {
             hp *= a.h;
           }
         }
-        T run[NV];
+        T run[NV], facs[NM];
 #pragma unroll
         for (int v = 0; v < NV; ++v) run[v] = J[v][0];
 #pragma unroll
@@ -209,8 +212,17 @@ struct Stage1D {
             best = (run[v] > best || run[v] != run[v]) ? run[v] : best;
           }
           const T fac = exp(-(bx * inv_h * invH * best) * dt);
+          facs[l] = fac;
+          if (!a.hybrid) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) ut[v][l] *= fac;
+            for (int v = 0; v < NV; ++v) ut[v][l] *= fac;
+          }
+        }
+        if (a.hybrid) {
+          // Algorithm 1: eta = (|[rho]_{j-1/2}| + |[rho]_{j+1/2}|) / (2 h); u^DG stored as it is
+          const T eta = J[0][0] * T(0.5) * inv_h;
+          hybrid_record<T, K>(a.hyb, a.ncell, xc, out_lane, eta, facs);
+          if (out_lane) my_eta = nan_max(eta, my_eta);
         }
       }
       if constexpr (EQ == EQ_EULER) {
@@ -232,6 +244,7 @@ struct Stage1D {
         }
       }
     }
+    if (a.hybrid) hybrid_max(a.hyb, my_eta);
   }
 
   // Max CFL rate beta / h over the positivity limiter's points of one cell (Gauss points and both

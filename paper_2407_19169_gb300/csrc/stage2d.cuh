@@ -42,6 +42,8 @@ struct Stage2DArgs {
   int H;             // rows per chunk
   int nstrips, nchunks;
   int positivity;    // Euler: Zhang-Shu limiter after the filter
+  int hybrid;        // hybrid limiter (Algorithm 1): store u^DG, eta and the filter factors
+  HybridOut hyb;
   DevScalars* sc;
 };
 
@@ -207,8 +209,9 @@ struct Stage2D {
   using ST = Store<PR, NV, NM>;
   using TB = Tab2D<K, BASIS>;
 
-  // per-warp shared memory: 3 row slots of u~ plus the partial damping Q[v][l-1] of one row
-  static constexpr size_t warp_bytes() { return sizeof(T) * (3 * NV * NME + NV * LMAX) * 32; }
+  // per-warp shared memory: 3 row slots of u~, the partial damping Q[v][l-1] of one row and the
+  // partial jump indicator of one row (hybrid limiter)
+  static constexpr size_t warp_bytes() { return sizeof(T) * (3 * NV * NME + NV * LMAX + 1) * 32; }
   static constexpr size_t slot_bytes_per_warp() { return warp_bytes(); }
 
   // ---- compile-time tables of the positivity limiter's points (evaluated by the front end) ----
@@ -522,6 +525,8 @@ struct Stage2D {
     const T dt = (T)dtd;
     const int lane = threadIdx.x & 31;
     T* wq = ws + 3 * NV * NME * 32;                               // Q[v][l-1] of the next row to filter
+    T* weta = wq + NV * LMAX * 32;                                // hybrid: eta of the next row, partial
+    T my_eta = T(0);
     const int nx = a.nx, ny = a.ny;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax, ay = (T)a.ay;
     const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy, c1dt = a.c1 * dtd;
@@ -733,7 +738,9 @@ struct Stage2D {
         T sig[LMAX + 1];
 #pragma unroll
         for (int l = 0; l <= LMAX; ++l) sig[l] = T(0);
+        T eta2 = T(0);                                            // hybrid: eta of row t-2
         if (a.filter_on && (need_v || filt_row)) {
+          T eta_v = T(0), eta_h = T(0);
           const int s1 = slot_of(t - 1), s2 = slot_of(t - 2);
 #pragma unroll 1
           for (int v = 0; v < NV; ++v) {
@@ -798,11 +805,22 @@ struct Stage2D {
             for (int l = 0; l <= LMAX; ++l) {
               shc += wy[l] * sh[l];
               if (need_v) av += wx[l] * (shfl_up_t(svr[l], 1) + svr[l]);
-              if (l == 0) continue;
+              if (l == 0) {
+                // density: edge-averaged value jumps, J^V / (2 h_x) and the face (t-2 | t-1) / (2 h_y)
+                if (a.hybrid && v == 0) {
+                  eta_v = av * T(0.5) * inv_hx;
+                  eta_h = shc * T(0.5) * inv_hy;
+                }
+                continue;
+              }
               T* q = wq + ((v * LMAX + (l - 1)) << 5) + lane;
               if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * shc);   // Q of row t-2 + its top face
               if (need_v) *q = bx1 * av + by1 * shc;                      // Q of row t-1 (bottom face)
             }
+          }
+          if (a.hybrid) {
+            if (filt_row) eta2 = weta[lane] + eta_h;             // row t-2: + its top face
+            if (need_v) weta[lane] = eta_v + eta_h;               // row t-1: vertical faces + bottom face
           }
         }
         if (filt_row) {
@@ -821,10 +839,16 @@ struct Stage2D {
             T fac[LMAX + 1];
 #pragma unroll
             for (int l = 1; l <= LMAX; ++l) fac[l] = exp(-(sig[l] * invH2) * dt);
+            if (a.hybrid) {
+              // u^DG is stored as it is; the blend kernel limits the troubled cells
+              hybrid_record<T, LMAX>(a.hyb, a.ncell, cell2, out_lane, eta2, fac);
+              if (out_lane) my_eta = nan_max(eta2, my_eta);
+            } else {
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+              for (int v = 0; v < NV; ++v)
 #pragma unroll
-              for (int m = 1; m < NM; ++m) uo[v][m] *= fac[PP[m] + QQ[m]];
+                for (int m = 1; m < NM; ++m) uo[v][m] *= fac[PP[m] + QQ[m]];
+            }
           }
           if (a.positivity && out_lane) positivity_limit(uo, gm1);
           if (out_lane) {
@@ -851,6 +875,7 @@ struct Stage2D {
         phys2 = phys1;
       }
     }
+    if (a.hybrid) hybrid_max(a.hyb, my_eta);
   }
 
   // Max CFL rate beta^x / hx + beta^y / hy over the positivity limiter's points of one cell: with

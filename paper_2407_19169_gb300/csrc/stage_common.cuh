@@ -98,4 +98,33 @@ __device__ __forceinline__ void stage_end(DevScalars* sc, int stage, double my_r
   }
 }
 
+// Hybrid limiter (Algorithm 1), one row of output cells of a warp: eta and the filter factors of the
+// lanes that own an output cell go to the scratch arrays, the troubled ones (eta > 1) are appended
+// to the list. Called by every lane of the warp (ballot).
+template <class T, int LMAX>
+__device__ __forceinline__ void hybrid_record(const HybridOut& h, long long ncell, long long cell, bool active,
+                                              T eta, const T (&fac)[LMAX + 1]) {
+  const int lane = threadIdx.x & 31;
+  if (active) {
+    ((T*)h.eta)[cell] = eta;
+#pragma unroll
+    for (int l = 1; l <= LMAX; ++l) ((T*)h.fac)[(long long)(l - 1) * ncell + cell] = fac[l];
+  }
+  const bool tr = active && eta > T(1);
+  const unsigned mask = __ballot_sync(0xffffffffu, tr);
+  if (mask) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&h.sc->count, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (tr) h.list[base + __popc(mask & ((1u << lane) - 1u))] = (int)cell;
+  }
+}
+
+// The warp's largest eta into the stage maximum (called by every lane).
+template <class T>
+__device__ __forceinline__ void hybrid_max(const HybridOut& h, T my_eta) {
+  const double m = warp_max((double)my_eta);
+  if ((threadIdx.x & 31) == 0 && !(m <= 0.0)) atomic_max_nonneg(&h.sc->max_bits, m);
+}
+
 }  // namespace dgk

@@ -1,0 +1,120 @@
+"""The hybrid limiter of Algorithm 1 on the GPU (stage kernel storing u^DG, eta and the filter factors;
+blend kernel over the troubled cells) against the oracle, through the C ABI, on data where cells are
+troubled; plus the reductions that hold exactly."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_19169_gb300 import _native as N
+from paper_2407_19169_gb300 import inputs as I
+
+from _helpers import rel_l1
+
+pytestmark = pytest.mark.gpu
+INF = float("inf")
+SOD = [1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 0.5]
+
+
+def tolerance(p, u0, uo, steps):
+    """1e-11, or 30x the oracle's own response to a 1-ulp perturbation of the input where the problem
+    amplifies roundoff beyond that (as in the plain parity tests)."""
+    rng = np.random.default_rng(1)
+    up = u0 * (1.0 + 1e-16 * rng.standard_normal(u0.shape))
+    ub, _, _ = O.advance(p, up, 0.0, INF, steps)
+    return max(1e-11, 30.0 * rel_l1(p, ub, uo))
+
+
+def solver(p, precision=N.PREC_FP64, hybrid=1, filt=1):
+    return N.Solver(dim=p.dim, nx=p.nx, ny=p.ny, x0=p.x0, x1=p.x1, y0=p.y0, y1=p.y1, bc=p.bc, k=p.k,
+                    eq=p.eq, precision=precision, hybrid=hybrid, filter=filt, tile_rows=8)
+
+
+def run(p, u0, steps, precision=N.PREC_FP64):
+    s = solver(p, precision)
+    s.write_state(u0)
+    s.advance_steps(steps)
+    st, t, n = s.sync()
+    assert st == 0 and n == steps
+    ug, tg = s.read_state()
+    s.close()
+    return ug, tg
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_sod_1d_matches_oracle(k):
+    p = O.Problem(dim=1, nx=230, x0=0.0, x1=1.0, k=k, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_RIEMANN1D, SOD)
+    assert O.jump_indicator(p, u0).max() > 1.0                  # troubled cells from the start
+    ug, tg = run(p, u0, 100)
+    uo, to, _ = O.advance(p, u0, 0.0, INF, 100)
+    assert abs(tg - to) <= 1e-12 * to
+    assert rel_l1(p, ug, uo) <= tolerance(p, u0, uo, 100)
+
+
+def test_seeded_riemann_1d_matches_oracle():
+    p = O.Problem(dim=1, nx=300, x0=0.0, x1=1.0, k=2, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_RIEMANN1D, I.riemann1d_params(2))
+    ug, _ = run(p, u0, 100)
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 100)
+    assert rel_l1(p, ug, uo) <= tolerance(p, u0, uo, 100)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_quadrant_2d_matches_oracle(k):
+    p = O.Problem(dim=2, nx=62, ny=36, k=k, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(1))
+    assert O.jump_indicator(p, u0).max() > 1.0
+    ug, _ = run(p, u0, 50)
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 50)
+    assert rel_l1(p, ug, uo) <= tolerance(p, u0, uo, 50)
+
+
+def test_fp32_form_sod_error_within_2_percent_of_fp64():
+    p = O.Problem(dim=1, nx=400, x0=0.0, x1=1.0, k=2, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_RIEMANN1D, SOD)
+    errs = []
+    for prec in (N.PREC_FP64, N.PREC_FP32_MIXED):
+        s = solver(p, prec)
+        s.write_state(u0)
+        s.advance_to(0.15)
+        u, t = s.read_state()
+        s.close()
+        errs.append(O.errors(p, u, O.EX_RIEMANN1D, SOD, t, var=0, nq_err=6)[0])
+    assert errs[1] <= 1.02 * errs[0], errs
+
+
+def test_nothing_troubled_is_plain_rkdg():
+    p = O.Problem(dim=2, nx=40, ny=30, x0=0.0, x1=10.0, y0=-5.0, y1=5.0, k=2, eq=O.EQ_EULER, hybrid=1)
+    u0 = O.project(p, O.IC_VORTEX2D, [5.0, 0.0, 5.0, 0.0])
+    assert O.jump_indicator(p, u0).max() < 1.0
+    a = solver(p, hybrid=1)
+    b = solver(p, hybrid=0, filt=0)
+    for s in (a, b):
+        s.write_state(u0)
+        s.advance_steps(20)
+        assert s.sync()[0] == 0
+    np.testing.assert_array_equal(a.read_state()[0], b.read_state()[0])
+
+
+def test_hybrid_rejected_where_unsupported():
+    with pytest.raises(N.DGError):
+        N.Solver(dim=1, nx=50, k=1, eq=N.EQ_EULER, hybrid=1, positivity=1)
+    with pytest.raises(N.DGError):
+        N.Solver(dim=1, nx=50, k=1, eq=N.EQ_EULER, hybrid=1, filter=0)
+    s = N.Solver(dim=1, nx=50, k=1, eq=N.EQ_EULER, hybrid=1, precision=N.PREC_FP32_MIXED)
+    assert N.batch_run([s], 1) == -8
+
+
+def test_launch_count_includes_the_blend_kernel():
+    p = O.Problem(dim=2, nx=60, ny=30, k=2, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(1))
+    for hyb, per_step in ((1, 6), (0, 3)):
+        s = solver(p, hybrid=hyb)
+        s.write_state(u0)
+        s.advance_steps(2)
+        assert s.sync()[0] == 0
+        l0 = s.kernel_launches()
+        s.advance_steps(10)                         # step pairs replayed from the captured graph
+        assert s.sync()[0] == 0
+        assert s.kernel_launches() - l0 == 10 * per_step
+        s.close()
