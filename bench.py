@@ -195,7 +195,7 @@ def make_instance(N, I, spec, stream, tiles):
     return s
 
 
-def run_batched(torch, N, stream, steps, n_inst):
+def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
     """S2: n_inst uneven instances (inputs.batched_specs), each advanced `steps` steps by dg_batch_run
     (one graph-captured work-list launch per class and stage); autotuned 2D tiles per degree; the
     positivity-preserving limiter after the filter, as the paper does for hard Riemann data."""
@@ -203,7 +203,8 @@ def run_batched(torch, N, stream, steps, n_inst):
     from paper_2407_19169_gb300 import tuning
     specs = I.batched_specs(n=n_inst, riemann_seeds=accepted("riemann1d_seeds.txt"),
                             quadrant_seeds=accepted("quadrant_seeds.txt"))
-    tiles = {k: tuning.tune_2d(256, 256, k=k) for k in (1, 2, 3)}
+    tiles = ({k: (tile_rows, 4) for k in (1, 2, 3)} if tile_rows else
+             {k: tuning.tune_2d(256, 256, k=k) for k in (1, 2, 3)})
     t0 = time.perf_counter()
     inst = [make_instance(N, I, sp, stream.cuda_stream, tiles) for sp in specs]
     setup_s = time.perf_counter() - t0
@@ -351,6 +352,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-tile-rows", type=int, default=0, help="2D tile rows of the batch (0 = autotuned)")
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--served-rate", type=float, default=10.0)
     ap.add_argument("--served-requests", type=int, default=12)
@@ -462,7 +464,7 @@ def main():
     value, ms32 = aggregate(torch, dist_mod, ms32, 3.0 * ndof * args.steps, world, "cuda")
 
     batched = None if args.skip_batched else run_batched(torch, N, stream, args.batched_steps,
-                                                         args.batched_instances)
+                                                         args.batched_instances, args.batched_tile_rows)
     served = None if args.skip_served else run_served(N, stream, args.served_rate, args.served_requests,
                                                       args.served_budget_gb * 1e9)
     if rank != 0:

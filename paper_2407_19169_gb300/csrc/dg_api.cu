@@ -179,7 +179,9 @@ static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
     if (!s->L.launch) return DG_ERR_UNSUPPORTED;
     s->nwarps1d = (s->mesh.nx + STRIP_OUT - 1) / STRIP_OUT;
     s->block = 128;
-    s->grid = (unsigned)((s->nwarps1d + 3) / 4);
+    // at most 8 blocks of 4 warps per SM (64 registers a thread); warps loop over strips
+    long long g1 = (s->nwarps1d + 3) / 4;
+    s->grid = (unsigned)(g1 < 152LL * 8 ? g1 : 152LL * 8);
     s->smem = 256;
     return DG_OK;
   }
@@ -496,6 +498,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.hybrid = s->hybrid;
       a.hyb = s->hy;
       a.sc = s->sc;
+      stage1d_consts(a);
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     } else {
       Stage2DArgs a;

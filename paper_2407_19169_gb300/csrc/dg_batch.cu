@@ -29,6 +29,9 @@ struct BatchInst {
   long long item0;     // first work item of this instance within its class
   int nx, ny, bcx, bcy, H, nstrips, nchunks, filter_on, positivity;
   double hx, hy, gamma, ax, ay, cfl;
+  // 1D mesh constants from the host (stage1d_consts)
+  double inv_h_d, scl_d, wpow_d[4];
+  float inv_h_f, scl_f, wpow_f[4];
 };
 
 struct BatchArgs {
@@ -36,6 +39,7 @@ struct BatchArgs {
   int ninst;
   long long nitems;
   int stage;
+  float c0_hi, c0_lo;      // the stage's c0 as a double-float
 };
 
 __device__ __forceinline__ int find_inst(const BatchInst* inst, int n, long long w) {
@@ -66,8 +70,25 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
   const int wib = threadIdx.x >> 5;
   T* ws = (T*)(dyn_smem + S::warp_bytes() * wib);
   const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + wib; w < b.nitems; w += nwt) {
-    const BatchInst& I = b.inst[find_inst(b.inst, b.ninst, w)];
+  // each warp takes a contiguous range of items, so consecutive items mostly belong to one
+  // instance and its rate / physicality are folded once per run of items, not once per item
+  const long long per = (b.nitems + nwt - 1) / nwt;
+  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + wib) * per;
+  const long long w1 = w0 + per < b.nitems ? w0 + per : b.nitems;
+  int cur = -1;
+  long long cur_step = 0;
+  double racc = 0.0;
+  bool okacc = true;
+  for (long long w = w0; w < w1; ++w) {
+    const int ii = find_inst(b.inst, b.ninst, w);
+    if (ii != cur) {
+      if (cur >= 0) item_end(b.inst[cur], b.stage, cur_step, racc, okacc);
+      cur = ii;
+      cur_step = ((volatile DevScalars*)b.inst[ii].sc)->step;
+      racc = 0.0;
+      okacc = true;
+    }
+    const BatchInst& I = b.inst[ii];
     volatile DevScalars* vs = I.sc;
     if (vs->done | vs->err) continue;
     const long long step = vs->step;
@@ -105,8 +126,11 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
     bool ok = true;
     S::item(a, dt, (int)(local % I.nstrips), (int)(local / I.nstrips), ws, r, rt, ok);
     if constexpr (PR::MIXED) r = (double)rt;
-    item_end(I, b.stage, step, r, ok);
+    (void)step;
+    racc = (r > racc || r != r) ? r : racc;
+    okacc = okacc && ok;
   }
+  if (cur >= 0) item_end(b.inst[cur], b.stage, cur_step, racc, okacc);
 }
 
 template <int K, int EQ, class PR>
@@ -114,8 +138,25 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
   using S = Stage1D<K, EQ, PR>;
   using T = typename PR::T;
   const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < b.nitems; w += nwt) {
-    const BatchInst& I = b.inst[find_inst(b.inst, b.ninst, w)];
+  // each warp takes a contiguous range of items, so consecutive items mostly belong to one
+  // instance and its rate / physicality are folded once per run of items, not once per item
+  const long long per = (b.nitems + nwt - 1) / nwt;
+  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per;
+  const long long w1 = w0 + per < b.nitems ? w0 + per : b.nitems;
+  int cur = -1;
+  long long cur_step = 0;
+  double racc = 0.0;
+  bool okacc = true;
+  for (long long w = w0; w < w1; ++w) {
+    const int ii = find_inst(b.inst, b.ninst, w);
+    if (ii != cur) {
+      if (cur >= 0) item_end(b.inst[cur], b.stage, cur_step, racc, okacc);
+      cur = ii;
+      cur_step = ((volatile DevScalars*)b.inst[ii].sc)->step;
+      racc = 0.0;
+      okacc = true;
+    }
+    const BatchInst& I = b.inst[ii];
     volatile DevScalars* vs = I.sc;
     if (vs->done | vs->err) continue;
     const long long step = vs->step;
@@ -141,13 +182,27 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
     a.hybrid = 0;
     a.hyb = HybridOut{};
     a.sc = I.sc;
+    a.inv_h_d = I.inv_h_d;
+    a.scl_d = I.scl_d;
+    a.inv_h_f = I.inv_h_f;
+    a.scl_f = I.scl_f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      a.wpow_d[m] = I.wpow_d[m];
+      a.wpow_f[m] = I.wpow_f[m];
+    }
+    a.c0_hi = b.c0_hi;
+    a.c0_lo = b.c0_lo;
     double r = 0.0;
     T rt = T(0);
     bool ok = true;
     S::item(a, dt, w - I.item0, r, rt, ok);
     if constexpr (PR::MIXED) r = (double)rt;
-    item_end(I, b.stage, step, r, ok);
+    (void)step;
+    racc = (r > racc || r != r) ? r : racc;
+    okacc = okacc && ok;
   }
+  if (cur >= 0) item_end(b.inst[cur], b.stage, cur_step, racc, okacc);
 }
 
 // Per-instance dt at the start of a step (the same rule as the single-solve stage 0).
@@ -275,6 +330,19 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
       I.ax = s->ax;
       I.ay = s->ay;
       I.cfl = s->cfl;
+      {
+        Stage1DArgs t{};
+        t.h = s->geom.hx;
+        stage1d_consts(t);
+        I.inv_h_d = t.inv_h_d;
+        I.scl_d = t.scl_d;
+        I.inv_h_f = t.inv_h_f;
+        I.scl_f = t.scl_f;
+        for (int m = 0; m < 4; ++m) {
+          I.wpow_d[m] = t.wpow_d[m];
+          I.wpow_f[m] = t.wpow_f[m];
+        }
+      }
       cls_items[c] += (long long)I.nstrips * I.nchunks;
       if (s->dim == 2 && s->warps_per_block < cls_wpb[c]) cls_wpb[c] = s->warps_per_block;
       host.push_back(I);
@@ -318,9 +386,14 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
         b.ninst = cls_count[c];
         b.nitems = cls_items[c];
         b.stage = stage;
+        {
+          const double c0 = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+          b.c0_hi = (float)c0;
+          b.c0_lo = (float)(c0 - (double)b.c0_hi);
+        }
         const int wpb = cls_wpb[c];
         long long blocks = (cls_items[c] + wpb - 1) / wpb;
-        if (blocks > 152LL * 4) blocks = 152LL * 4;
+        if (blocks > 152LL * 4) blocks = 152LL * 4;   // warps then take contiguous item ranges
         ce = cudaStreamWaitEvent(side[c], fork, 0);
         if (ce == cudaSuccess)
           ce = BL[c].launch(b, (unsigned)blocks, 32u * wpb, BL[c].warp_bytes * wpb, side[c]);

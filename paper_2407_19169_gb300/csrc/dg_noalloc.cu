@@ -143,6 +143,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.hybrid = 0;
       a.hyb = HybridOut{};
       a.sc = sc;
+      stage1d_consts(a);
       if (L.launch(&a, (unsigned)((nwarps + 3) / 4), 128, 256, st) != cudaSuccess) return DG_ERR_CUDA;
     }
   } else {

@@ -35,7 +35,28 @@ struct Stage1DArgs {
   int hybrid;        // hybrid limiter (Algorithm 1): store u^DG, eta and the filter factors
   HybridOut hyb;
   DevScalars* sc;
+  // mesh constants computed once on the host (stage1d_consts): 1/h, 2/h and the jump weights
+  // m(m+1) h^m (1 for m = 0), in both arithmetic types; c0 as a double-float
+  double inv_h_d, scl_d, wpow_d[4];
+  float inv_h_f, scl_f, wpow_f[4];
+  float c0_hi, c0_lo;
 };
+
+// Fill the host-side constants of a Stage1DArgs from its h and c0 (no FP64 division on the GPU).
+inline void stage1d_consts(Stage1DArgs& a) {
+  a.inv_h_d = 1.0 / a.h;
+  a.scl_d = 2.0 / a.h;
+  a.inv_h_f = (float)a.inv_h_d;
+  a.scl_f = (float)a.scl_d;
+  double hp = 1.0;
+  for (int m = 0; m < 4; ++m) {
+    a.wpow_d[m] = m == 0 ? 1.0 : m * (m + 1) * hp;
+    a.wpow_f[m] = (float)a.wpow_d[m];
+    hp *= a.h;
+  }
+  a.c0_hi = (float)a.c0;
+  a.c0_lo = (float)(a.c0 - (double)a.c0_hi);
+}
 
 template <int K, int EQ, class PR>
 struct Stage1D {
@@ -45,6 +66,7 @@ struct Stage1D {
   static constexpr int NQ = K + 1;
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
+  using TB = Tab2D<K, BASIS_Q>;        // the 1D mode l is the x-degree p of the tables
 
   static __device__ __forceinline__ T sd(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ T su(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
@@ -57,10 +79,22 @@ struct Stage1D {
     const int lane = threadIdx.x & 31;
     const int nx = a.nx;
     const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax;
-    const T inv_h = (T)(1.0 / a.h), scl = (T)(2.0 / a.h);
+    T inv_h, scl, wpow[NM];
+    if constexpr (PR::MIXED) {
+      inv_h = a.inv_h_f;
+      scl = a.scl_f;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) wpow[m] = a.wpow_f[m];
+    } else {
+      inv_h = a.inv_h_d;
+      scl = a.scl_d;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) wpow[m] = a.wpow_d[m];
+    }
+    const T c1dt = (T)(a.c1 * dtd), c0 = (T)a.c0;
     // double-float coefficients of the cell-average update (once per item, off the cell path)
-    const df dcf = df_from_double(a.c1 * dtd / a.h);
-    const df dc0 = df_from_double(a.c0);
+    const df dcf = df_from_double(a.c1 * dtd * a.inv_h_d);
+    const df dc0 = df{a.c0_hi, a.c0_lo};
     T my_eta = T(0);
     {
       const int x = (int)strip * STRIP_OUT - 2 + lane;
@@ -104,22 +138,28 @@ struct Stage1D {
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int l = 0; l < NM; ++l) acc[v][l] = T(0);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
+      sfor<NQ>([&](auto Q_) {
+        constexpr int q = decltype(Q_)::value;
         T uq[NV], fq[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          T s = T(0);
-#pragma unroll
-          for (int l = 0; l < NM; ++l) s += u[v][l] * (T)GR::P(l, q);
+          T s = u[v][0];
+          sfor<NM>([&](auto L_) {
+            constexpr int l = decltype(L_)::value;
+            constexpr double c = TB::GP[l * NQ + q];
+            if constexpr (l >= 1 && c != 0.0) s += u[v][l] * (T)c;
+          });
           uq[v] = s;
         }
         flux1d<EQ>(uq, fq, gm1, ax);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-#pragma unroll
-          for (int l = 1; l < NM; ++l) acc[v][l] += fq[v] * (T)(GR::w(q) * GR::dP(l, q));
-      }
+          sfor<NM>([&](auto L_) {
+            constexpr int l = decltype(L_)::value;
+            constexpr double c = TB::WD[l * NQ + q];
+            if constexpr (l >= 1 && c != 0.0) acc[v][l] += fq[v] * (T)c;
+          });
+      });
       T un_[NV][NM], unlo[NV];
       if (a.stage > 0) ST::load(a.un, a.ncell, xc, un_, unlo);
       T ut[NV][NM], ulo[NV];
@@ -131,8 +171,8 @@ struct Stage1D {
           if (PR::MIXED && l == 0) continue;
           // u~ = u + c0 (u^n - u) + c1 dt R: equal to c0 u^n + c1 (u + dt R) when c0 + c1 = 1, and
           // it keeps that identity exact whatever the rounding of c0 and c1
-          T val = u[v][l] + (T)a.c1 * dt * R;
-          if (a.stage > 0) val += (T)a.c0 * (un_[v][l] - u[v][l]);
+          T val = u[v][l] + c1dt * R;
+          if (a.stage > 0) val += c0 * (un_[v][l] - u[v][l]);
           ut[v][l] = val;
         }
         ulo[v] = T(0);
@@ -171,35 +211,30 @@ struct Stage1D {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           T jr[NM];
-#pragma unroll
-          for (int r = 0; r < NM; ++r) {
-            T dl = T(0), dr = T(0);
-#pragma unroll
-            for (int l = r; l < NM; ++l) {
-              dl += ut[v][l] * (T)dend(0, l, r);
-              dr += ut[v][l] * (T)dend(1, l, r);
-            }
-            T f = T(1);
-#pragma unroll
-            for (int i = 0; i < r; ++i) f *= scl;
+          T f = T(1);                              // (2/h)^r
+          sfor<NM>([&](auto R_) {
+            constexpr int r = decltype(R_)::value;
+            // d^r u~ at xi = +1 and -1: P_l^{(r)}(-1) = (-1)^{l+r} P_l^{(r)}(+1)
+            T ev = T(-0.0), od = T(-0.0);
+            sfor<NM>([&](auto L_) {
+              constexpr int l = decltype(L_)::value;
+              constexpr double c = TB::DE[l * (K + 1) + r];
+              if constexpr (l >= r && c != 0.0) {
+                if constexpr ((l & 1) != 0) od += ut[v][l] * (T)c;
+                else ev += ut[v][l] * (T)c;
+              }
+            });
+            T dr = ev + od, dl = ((r & 1) != 0) ? od - ev : ev - od;
+            if constexpr (r > 0) f *= scl;
             dl *= f;
             dr *= f;
             const T nbl = sd(dl, 1);
             jr[r] = fabs(nbl - dr);
-          }
+          });
 #pragma unroll
           for (int r = 0; r < NM; ++r) J[v][r] = su(jr[r], 1) + jr[r];
         }
         // sigma^l = beta / (h Hbar) max_v (J_0 + sum_{m<=l} m(m+1) h^m J_m)
-        T wpow[NM];
-        {
-          double hp = 1.0;
-#pragma unroll
-          for (int m = 0; m < NM; ++m) {
-            wpow[m] = (T)(m == 0 ? 1.0 : m * (m + 1) * hp);
-            hp *= a.h;
-          }
-        }
         T run[NV], facs[NM];
 #pragma unroll
         for (int v = 0; v < NV; ++v) run[v] = J[v][0];
@@ -251,6 +286,7 @@ struct Stage1D {
   // ends): with the limiter on, Zhang and Shu's positivity result for the averages needs the CFL
   // bound on the wave speeds at those points.
   static __device__ T point_rate(const T (&ut)[NV][NM], T gam, T gm1, double h) {
+    constexpr carr<double, (K + 1) * NQ> GPT = TB::GP;
     T best = T(0);
     if constexpr (EQ == EQ_EULER) {
       constexpr int NP = NQ + 2;
@@ -263,7 +299,7 @@ struct Stage1D {
           T x = T(0);
 #pragma unroll
           for (int l = 0; l < NM; ++l) {
-            const double c = i < NQ ? GR::P(l, i) : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
+            const double c = i < NQ ? GPT[l * NQ + i] : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
             x += (T)c * ut[v][l];
           }
           w[v] = x;
@@ -280,6 +316,7 @@ struct Stage1D {
   // Zhang-Shu positivity-preserving limiter on one cell (after the filter, Section 3.2 of the
   // paper), checked at the Gauss points and both ends; averages untouched.
   static __device__ void positivity_limit(T (&ut)[NV][NM], T gm1) {
+    constexpr carr<double, (K + 1) * NQ> GPT = TB::GP;
     if constexpr (EQ == EQ_EULER) {
       constexpr int NP = NQ + 2;
       T ub[NV];
@@ -297,7 +334,7 @@ struct Stage1D {
       eps = pbar < eps ? pbar : eps;
       if (!(eps > T(0)) || !(eps_r > T(0))) return;
       auto coef = [&](int i, int l) -> double {
-        return i < NQ ? GR::P(l, i) : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
+        return i < NQ ? GPT[l * NQ + i] : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
       };
       T rmin = ub[0];
 #pragma unroll
@@ -343,10 +380,13 @@ struct Stage1D {
     if (!ctl.run) return;
     double* red = (double*)smem;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
     double my_rate = 0.0;
     T my_rate_t = T(0);
     bool my_ok = true;
-    if (gw < a.nwarps) item(a, ctl.dt, gw, my_rate, my_rate_t, my_ok);
+    // a bounded grid: each warp takes strips gw, gw + nwt, ... so the per-block step control and
+    // rate reduction are paid once per block, not once per 28 cells
+    for (long long w = gw; w < a.nwarps; w += nwt) item(a, ctl.dt, w, my_rate, my_rate_t, my_ok);
     if constexpr (PR::MIXED) my_rate = (double)my_rate_t;
     stage_end(a.sc, a.stage, my_rate, my_ok, red);
   }

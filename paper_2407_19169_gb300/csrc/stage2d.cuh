@@ -108,93 +108,6 @@ struct Store {
   }
 };
 
-// Compile-time tables of the tensor-product sum factorisation for degree K, basis BASIS (P^k drops
-// the modes p + q > k). All are evaluated by the compiler front end and read only in constant
-// expressions, so every coefficient the kernels multiply by is an immediate.
-template <int K, int BASIS>
-struct Tab2DBuild {
-  using MB = Modes<K, BASIS>;
-  using GR = GaussRule<K + 1>;
-  static constexpr int NQ = K + 1;
-  static constexpr int NM = MB::NM;
-
-  static constexpr carr<int, (K + 1) * (K + 1)> mi() {
-    carr<int, (K + 1) * (K + 1)> t{};
-    for (int i = 0; i < (K + 1) * (K + 1); ++i) t[i] = -1;
-    for (int m = 0; m < NM; ++m) t[MB::p(m) * (K + 1) + MB::q(m)] = m;
-    return t;
-  }
-  static constexpr carr<int, NM> pq(int which) {
-    carr<int, NM> t{};
-    for (int m = 0; m < NM; ++m) t[m] = which == 0 ? MB::p(m) : MB::q(m);
-    return t;
-  }
-  // [l * NQ + g]: P_l(x_g) (0), w_g P_l(x_g) (1), w_g P_l'(x_g) (2)
-  static constexpr carr<double, (K + 1) * NQ> gauss(int which) {
-    carr<double, (K + 1) * NQ> t{};
-    for (int l = 0; l <= K; ++l)
-      for (int g = 0; g < NQ; ++g)
-        t[l * NQ + g] = which == 0 ? GR::P(l, g) : (which == 1 ? GR::w(g) * GR::P(l, g) : GR::w(g) * GR::dP(l, g));
-    return t;
-  }
-  // [l * (K + 1) + r]: P_l^{(r)}(+1), zero for r > l
-  static constexpr carr<double, (K + 1) * (K + 1)> ends() {
-    carr<double, (K + 1) * (K + 1)> t{};
-    for (int l = 0; l <= K; ++l)
-      for (int r = 0; r <= K; ++r) t[l * (K + 1) + r] = dend(1, l, r);
-    return t;
-  }
-  static constexpr carr<double, NM> minv() {
-    carr<double, NM> t{};
-    for (int m = 0; m < NM; ++m) t[m] = 0.5 * (2 * MB::p(m) + 1) * (2 * MB::q(m) + 1);
-    return t;
-  }
-};
-
-template <int K, int BASIS>
-struct Tab2D {
-  using B = Tab2DBuild<K, BASIS>;
-  static constexpr int NQ = K + 1;
-  static constexpr int NM = B::NM;
-  static constexpr carr<int, (K + 1) * (K + 1)> MIX = B::mi();
-  static constexpr carr<int, NM> PP = B::pq(0);
-  static constexpr carr<int, NM> QQ = B::pq(1);
-  static constexpr carr<double, (K + 1) * NQ> GP = B::gauss(0);
-  static constexpr carr<double, (K + 1) * NQ> WP = B::gauss(1);
-  static constexpr carr<double, (K + 1) * NQ> WD = B::gauss(2);
-  static constexpr carr<double, (K + 1) * (K + 1)> DE = B::ends();
-  static constexpr carr<double, NM> MINV = B::minv();
-
-  static constexpr bool has(int p, int q) { return p <= K && q <= K && MIX[p * (K + 1) + q] >= 0; }
-  // a mode (p, q) with q of parity `par` (p fixed) / p of parity `par` (q fixed), index >= 1
-  static constexpr bool any_q_par(int p, int par) {
-    for (int q = 1; q <= K; ++q)
-      if ((q & 1) == par && has(p, q)) return true;
-    return false;
-  }
-  static constexpr bool any_p_par(int q, int par) {
-    for (int p = 1; p <= K; ++p)
-      if ((p & 1) == par && has(p, q)) return true;
-    return false;
-  }
-  // sum_q u[p,q] P_q^{(a2)}(+1) has terms of parity par in q (q >= a2)
-  static constexpr bool hq(int p, int a2, int par) {
-    for (int q = a2; q <= K; ++q)
-      if ((q & 1) == par && has(p, q) && DE[q * (K + 1) + a2] != 0.0) return true;
-    return false;
-  }
-  // the x-polynomial H[p][a2] exists (some q >= a2 with mode (p, q))
-  static constexpr bool hh(int p, int a2) { return hq(p, a2, 0) || hq(p, a2, 1); }
-  // sum_p H[p][a2] P_p^{(a1)}(+1) has terms of parity par in p
-  static constexpr bool hp(int a1, int a2, int par) {
-    for (int p = a1; p <= K; ++p)
-      if ((p & 1) == par && hh(p, a2) && DE[p * (K + 1) + a1] != 0.0) return true;
-    return false;
-  }
-  // derivative multi-indices alpha = (a1, a2) that can be nonzero
-  static constexpr bool alpha_ok(int a1, int a2) { return BASIS == BASIS_Q ? true : a1 + a2 <= K; }
-};
-
 template <int K, int EQ, int BASIS, class PR>
 struct Stage2D {
   using T = typename PR::T;
