@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
     bool ok = true;
     S::item(a, dt, (int)(local % I.nstrips), (int)(local / I.nstrips), ws, r, rt, ok);
     if constexpr (PR::MIXED) r = (double)rt;
-    (void)step;
     racc = (r > racc || r != r) ? r : racc;
     okacc = okacc && ok;
   }
@@ -198,7 +197,6 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
     bool ok = true;
     S::item(a, dt, w - I.item0, r, rt, ok);
     if constexpr (PR::MIXED) r = (double)rt;
-    (void)step;
     racc = (r > racc || r != r) ? r : racc;
     okacc = okacc && ok;
   }

@@ -178,15 +178,18 @@ struct Stage1D {
         ulo[v] = T(0);
         if constexpr (PR::MIXED) {
           // cell average in double-float: u0 + c0 (un0 - u0) + c1 dt/h (F_L - F_R)
-          df m0{u[v][0], lo0[v]};
+          // (a cascaded double-float sum; the face terms are formed bitwise alike on both sides)
+          df_acc m0{u[v][0], lo0[v]};
           if (a.stage > 0) {
-            const df d = df_add(df{un_[v][0], unlo[v]}, df{-u[v][0], -lo0[v]});
-            m0 = df_add(m0, df_mul(dc0, d));
+            df_acc d{un_[v][0], unlo[v]};
+            d.add(df{-u[v][0], -lo0[v]});
+            m0.add(df_mul(dc0, d.result()));
           }
-          m0 = df_add(m0, df_mul_f(dcf, FL[v]));
-          m0 = df_add(m0, df_mul_f(dcf, -FR[v]));
-          ut[v][0] = m0.hi;
-          ulo[v] = m0.lo;
+          m0.add_prod(dcf, FL[v]);
+          m0.add_prod(dcf, -FR[v]);
+          const df r0 = m0.result();
+          ut[v][0] = r0.hi;
+          ulo[v] = r0.lo;
         }
       }
       T ub[NV];
