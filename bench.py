@@ -230,6 +230,34 @@ def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
             "gpu_launches": launches, "dtype": "f32+df64", "positivity_limiter": True}
 
 
+def run_small_configs(torch, N, stream, barrier):
+    """The two small workloads of the method: Burgers 0.5 + sin(pi x) on [0, 2], 200 cells, P2, FP64;
+    1D Euler seeded Riemann data, 65,536 cells, P3, FP64 and FP32 form. At these sizes a stage is a
+    few microseconds of work, so the figures show the graph-replayed launch rate."""
+    from paper_2407_19169_gb300 import inputs as I
+    out = {}
+    cases = [("burgers1d_p2_200", dict(dim=1, nx=200, x0=0.0, x1=2.0, k=2, eq=N.EQ_BURGERS,
+                                       bc=(N.BC_PERIODIC,) * 4), (N.IC_SINE, [0.5, 1.0, math.pi, 0.0]),
+              (N.PREC_FP64,), 2000),
+             ("euler1d_p3_65536", dict(dim=1, nx=65536, x0=0.0, x1=1.0, k=3, eq=N.EQ_EULER,
+                                       bc=(N.BC_OUTFLOW,) * 4),
+              (N.IC_RIEMANN1D, I.riemann1d_params(accepted("riemann1d_seeds.txt")[0])),
+              (N.PREC_FP64, N.PREC_FP32_MIXED), 2000)]
+    for name, kw, (ic, prm), precs, steps in cases:
+        for prec in precs:
+            s = N.Solver(precision=prec, stream=stream.cuda_stream, **kw)
+            s.set_initial(ic, prm)
+            s.advance_steps(10)
+            torch.cuda.synchronize()
+            ms, _ = time_steps(torch, s, steps, stream, barrier)
+            nv, nm, nc = s.shape
+            out["%s_%s" % (name, "f64" if prec == N.PREC_FP64 else "f32")] = {
+                "value": 3.0 * nv * nm * nc * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+                "us_per_step": 1e3 * ms / steps}
+            s.close()
+    return out
+
+
 def run_served(N, stream, rate, n_req, budget):
     """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching."""
     from paper_2407_19169_gb300 import serve as S
@@ -354,6 +382,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-tile-rows", type=int, default=0, help="2D tile rows of the batch (0 = autotuned)")
     ap.add_argument("--skip-served", action="store_true")
+    ap.add_argument("--skip-small", action="store_true")
     ap.add_argument("--served-rate", type=float, default=10.0)
     ap.add_argument("--served-requests", type=int, default=12)
     ap.add_argument("--served-budget-gb", type=float, default=120.0)
@@ -467,6 +496,7 @@ def main():
                                                          args.batched_instances, args.batched_tile_rows)
     served = None if args.skip_served else run_served(N, stream, args.served_rate, args.served_requests,
                                                       args.served_budget_gb * 1e9)
+    small = None if args.skip_small else run_small_configs(torch, N, stream, barrier)
     if rank != 0:
         return
     line = {
@@ -490,6 +520,7 @@ def main():
         "hybrid": hybrid,
         "batched": batched,
         "served": served,
+        "small_configs": small,
     }
     if not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(128 if nx >= 128 else nx, args.cpu_seconds, seed)

@@ -118,3 +118,35 @@ def test_launch_count_includes_the_blend_kernel():
         assert s.sync()[0] == 0
         assert s.kernel_launches() - l0 == 10 * per_step
         s.close()
+
+
+def test_fp32_form_2d_quadrant_close_to_oracle():
+    # FP32 stage arithmetic: the blend decisions are continuous in eta, so the FP32 form stays within
+    # FP32 roundoff growth of the FP64 oracle over a short run with troubled cells
+    p = O.Problem(dim=2, nx=60, ny=44, k=2, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(1))
+    ug, _ = run(p, u0, 20, precision=N.PREC_FP32_MIXED)
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 20)
+    assert rel_l1(p, ug, uo) <= 2e-5
+
+
+def test_p_basis_2d_matches_oracle():
+    p = O.Problem(dim=2, nx=50, ny=34, k=2, basis=O.BASIS_P, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4,
+                  hybrid=1)
+    u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(4))
+    s = N.Solver(dim=2, nx=50, ny=34, k=2, basis=N.BASIS_P, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4,
+                 hybrid=1, tile_rows=8)
+    s.write_state(u0)
+    s.advance_steps(40)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 40)
+    assert rel_l1(p, ug, uo) <= tolerance(p, u0, uo, 40)
+
+
+def test_fp32_form_1d_close_to_oracle():
+    p = O.Problem(dim=1, nx=300, x0=0.0, x1=1.0, k=3, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4, hybrid=1)
+    u0 = O.project(p, O.IC_RIEMANN1D, SOD)
+    ug, _ = run(p, u0, 50, precision=N.PREC_FP32_MIXED)
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 50)
+    assert rel_l1(p, ug, uo) <= 2e-5
