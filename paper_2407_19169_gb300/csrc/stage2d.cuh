@@ -655,8 +655,8 @@ struct Stage2D {
         if (a.filter_on && (need_v || filt_row)) {
           T eta_v = T(0), eta_h = T(0);
           const int s1 = slot_of(t - 1), s2 = slot_of(t - 2);
-#pragma unroll 1
-          for (int v = 0; v < NV; ++v) {
+#pragma unroll(PR::MIXED ? NV : 1)
+          for (int v = 0; v < NV; ++v) {                        // FP32 form: the variables' chains interleave
             T uv[NM], u2[NM];
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
