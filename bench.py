@@ -258,17 +258,18 @@ def run_small_configs(torch, N, stream, barrier):
     return out
 
 
-def run_served(N, stream, rate, n_req, budget):
+def run_served(N, stream, rate, n_req, budget, policy="srpt"):
     """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching."""
     from paper_2407_19169_gb300 import serve as S
     reqs = S.poisson_requests(rate=rate, n=n_req, seed=5, seeds=accepted("quadrant_seeds.txt"))
-    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream, positivity=1)
+    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream, positivity=1, policy=policy)
     t0 = time.perf_counter()
     results, stats = eng.run(reqs)
     wall = time.perf_counter() - t0
     out = S.summarize(results, wall)
     out.update({"rate_per_s": rate, "requests": n_req, "budget_gb": budget / 1e9, **stats,
-                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form", "positivity_limiter": True})
+                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form", "positivity_limiter": True,
+                "policy": policy})
     return out
 
 
@@ -383,6 +384,8 @@ def main():
     ap.add_argument("--batched-tile-rows", type=int, default=0, help="2D tile rows of the batch (0 = autotuned)")
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--skip-small", action="store_true")
+    ap.add_argument("--served-policy", default="srpt", choices=["srpt", "all"],
+                    help="which resident solves each round advances (serve.Engine)")
     ap.add_argument("--served-rate", type=float, default=10.0)
     ap.add_argument("--served-requests", type=int, default=12)
     ap.add_argument("--served-budget-gb", type=float, default=120.0)
@@ -495,7 +498,7 @@ def main():
     batched = None if args.skip_batched else run_batched(torch, N, stream, args.batched_steps,
                                                          args.batched_instances, args.batched_tile_rows)
     served = None if args.skip_served else run_served(N, stream, args.served_rate, args.served_requests,
-                                                      args.served_budget_gb * 1e9)
+                                                      args.served_budget_gb * 1e9, args.served_policy)
     small = None if args.skip_small else run_small_configs(torch, N, stream, barrier)
     if rank != 0:
         return

@@ -2,9 +2,15 @@
 
 Requests (2D Euler Q2 four-quadrant Riemann solves of different mesh sizes and end times) arrive
 as a Poisson stream. The engine keeps every admitted solve's state resident on the GPU and advances
-all of them together with dg_batch_run in chunks of a few steps; at every chunk boundary it retires
-the solves that reached their end time (each stops exactly at its own T) and admits waiting
-requests while the device-memory budget allows. Latency = completion time - arrival time.
+them with dg_batch_run in chunks of a few steps; at every chunk boundary it retires the solves that
+reached their end time (each stops exactly at its own T) and admits waiting requests while the
+device-memory budget allows. Latency = completion time - arrival time.
+
+Which resident solves a round advances is the scheduling policy: "all" advances every one; "srpt"
+(shortest remaining work first) advances the solves with the least estimated remaining work,
+(T - t) * side^3 (steps grow with side / CFL, cells with side^2), adding them until they cover
+`fill_cells` cells, enough to occupy the GPU, so short requests are not held behind long ones while
+the device stays busy.
 """
 from __future__ import annotations
 
@@ -69,7 +75,7 @@ class Engine:
     """
 
     def __init__(self, budget_bytes=120e9, chunk_steps=16, precision=N.PREC_FP32_MIXED, stream=None,
-                 keep_states=False, max_active=512, positivity=1):
+                 keep_states=False, max_active=512, positivity=1, policy="srpt", fill_cells=1 << 19):
         self.budget = budget_bytes
         self.chunk = chunk_steps
         self.precision = precision
@@ -77,6 +83,8 @@ class Engine:
         self.keep = keep_states
         self.max_active = max_active
         self.positivity = positivity
+        self.policy = policy
+        self.fill_cells = fill_cells
 
     def _bytes(self, req):
         return N.Solver.workspace_size(dim=2, nx=req.side, ny=req.side, bc=(N.BC_OUTFLOW,) * 4, k=2,
@@ -88,6 +96,7 @@ class Engine:
                      stream=self.stream, positivity=self.positivity)
         s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(req.seed))
         s.set_target(req.T)
+        s.last_t = 0.0
         return s
 
     def run(self, requests, clock=time.perf_counter):
@@ -113,10 +122,19 @@ class Engine:
             if not active:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
                 continue
-            st = N.batch_run([a[1] for a in active], self.chunk)
+            if self.policy == "srpt":
+                rem = [(req.T - s.last_t) * req.side ** 3 for req, s, adm, need in active]
+                pick = pick_round(rem, [req.side * req.side for req, s, adm, need in active], self.fill_cells)
+            else:
+                pick = list(range(len(active)))
+            st = N.batch_run([active[i][1] for i in pick], self.chunk)
             still = []
-            for req, s, adm, need in active:
+            for idx, (req, s, adm, need) in enumerate(active):
+                if idx not in pick:
+                    still.append((req, s, adm, need))
+                    continue
                 status, t, steps = s.sync()
+                s.last_t = t
                 if status != 0 or t >= req.T:
                     state = None
                     if self.keep and status == 0:
@@ -132,6 +150,19 @@ class Engine:
             active = still
             del st
         return results, {"peak_active": peak_active, "peak_bytes": peak_bytes}
+
+
+def pick_round(remaining, cells, fill_cells):
+    """Indices of the solves one round advances under shortest-remaining-work-first: ascending
+    estimated remaining work, until their cells reach fill_cells (all of them if they never do)."""
+    order = sorted(range(len(remaining)), key=lambda i: (remaining[i], i))
+    chosen, total = [], 0
+    for i in order:
+        chosen.append(i)
+        total += cells[i]
+        if total >= fill_cells:
+            break
+    return sorted(chosen)
 
 
 def summarize(results, wall):

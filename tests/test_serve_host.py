@@ -24,3 +24,13 @@ def test_summary_percentiles():
     s = S.summarize(rs, 100.0)
     assert s["p50_s"] == 50.0 and s["p99_s"] == 99.0 and s["completed"] == 100
     assert abs(s["dof_stage_per_s"] - 3.0 * 100 * 10 * 100 / 100.0) < 1e-9
+
+
+def test_srpt_round_picks_shortest_until_the_gpu_is_filled():
+    remaining = [50.0, 1.0, 7.0, 3.0, 100.0]
+    cells = [1 << 20, 1 << 14, 1 << 16, 1 << 16, 1 << 20]
+    # the three shortest hold 2^14 + 2 * 2^16 cells < 2^19: the next shortest (50) completes the fill
+    assert S.pick_round(remaining, cells, 1 << 19) == [0, 1, 2, 3]
+    assert S.pick_round(remaining, cells, 1 << 15) == [1, 3]
+    assert S.pick_round(remaining, cells, 1 << 40) == [0, 1, 2, 3, 4]
+    assert S.pick_round([2.0, 2.0], [10, 10], 5) == [0]           # ties: the earlier request
