@@ -763,19 +763,28 @@ struct Stage2D {
                 for (int m = 1; m < NM; ++m) uo[v][m] *= fac[PP[m] + QQ[m]];
             }
           }
-          if (a.positivity && out_lane) positivity_limit(uo, gm1);
+          T rate_pts = T(0);
+          if constexpr (K >= 3) {
+            if (a.positivity && out_lane) rate_pts = limit_and_rate(uo, gam, gm1, a.hx, a.hy);
+          } else {
+            if (a.positivity && out_lane) positivity_limit(uo, gm1);
+          }
           if (out_lane) {
             ST::store(a.uout, a.ncell, cell2, uo, lo);
             if (!phys2) my_ok = false;
             if constexpr (PR::MIXED) {
               const T r = bx2 * inv_hx + by2 * inv_hy;
               my_rate_t = nan_max(r, my_rate_t);
-              if (a.positivity) my_rate_t = nan_max(point_rate(uo, gam, gm1, a.hx, a.hy), my_rate_t);
+              if constexpr (K >= 3) {
+                if (a.positivity) my_rate_t = nan_max(rate_pts, my_rate_t);
+              } else {
+                if (a.positivity) my_rate_t = nan_max(point_rate(uo, gam, gm1, a.hx, a.hy), my_rate_t);
+              }
             } else {
               const double r = (double)bx2 / a.hx + (double)by2 / a.hy;
               my_rate = (r > my_rate || r != r) ? r : my_rate;
               if (a.positivity) {
-                const double rp = (double)point_rate(uo, gam, gm1, a.hx, a.hy);
+                const double rp = K >= 3 ? (double)rate_pts : (double)point_rate(uo, gam, gm1, a.hx, a.hy);
                 my_rate = (rp > my_rate || rp != rp) ? rp : my_rate;
               }
             }
@@ -894,6 +903,83 @@ struct Stage2D {
 #pragma unroll
           for (int m = 1; m < NM; ++m) uo[v][m] *= th2;
       }
+    }
+  }
+
+  // The limiter of positivity_limit with the CFL rate of point_rate taken in its pressure pass (the
+  // point values there are the final ones unless theta_2 < 1, in which case the limited cell is
+  // evaluated once more). Used from degree 3, where the points are many (NQ^2 + 4 NQ = 32).
+  static __device__ T limit_and_rate(T (&uo)[NV][NM], T gam, T gm1, double hx, double hy) {
+    if constexpr (EQ != EQ_EULER) {
+      return T(0);
+    } else {
+      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
+      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
+      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
+      constexpr int NP = NQ * NQ + 4 * NQ;
+      T ub[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ub[v] = uo[v][0];
+      const T pbar = pressure_of<NV>(ub, gm1);
+      // the same admissibility margins as positivity_limit
+      T eps_r = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * ub[0];
+      T eps = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * (ub[0] + fabs(ub[NV - 1]));
+      eps_r = ub[0] < eps_r ? ub[0] : eps_r;
+      eps = ub[0] < eps ? ub[0] : eps;
+      eps = pbar < eps ? pbar : eps;
+      if (!(eps > T(0)) || !(eps_r > T(0))) return point_rate(uo, gam, gm1, hx, hy);
+      const T thx = (T)hx, thy = (T)hy;
+      auto coef = [&](int i, int m) -> double {
+        return i < NQ * NQ ? VE[i * NM + m]
+                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
+      };
+      T rmin = ub[0];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T r = T(0);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const double c = coef(i, m);
+          if (c != 0.0) r += (T)c * uo[0][m];
+        }
+        rmin = r < rmin ? r : rmin;
+      }
+      if (rmin < eps_r) {
+        const T th1 = (ub[0] - eps_r) / (ub[0] - rmin);
+#pragma unroll
+        for (int m = 1; m < NM; ++m) uo[0][m] *= th1;
+      }
+      T th2 = T(1), rate = T(0);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T x = T(0);
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            const double c = coef(i, m);
+            if (c != 0.0) x += (T)c * uo[v][m];
+          }
+          w[v] = x;
+        }
+        if (pressure_of<NV>(w, gm1) < eps) {
+          const T t = pp_segment<NV>(ub, w, eps, gm1);
+          th2 = t < th2 ? t : th2;
+        }
+        T bx, by, invH;
+        bool ph;
+        avg_params<EQ, 2>(w, gam, gm1, T(0), T(0), bx, by, invH, ph);
+        rate = nan_max(bx / thx + by / thy, rate);
+      }
+      if (th2 < T(1)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int m = 1; m < NM; ++m) uo[v][m] *= th2;
+        rate = point_rate(uo, gam, gm1, hx, hy);
+      }
+      return rate;
     }
   }
 

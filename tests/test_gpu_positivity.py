@@ -20,7 +20,7 @@ def _pair2d(n, k, precision=N.PREC_FP64):
     return p, s
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_quadrant_seed3_with_limiter_matches_oracle(k):
     p, s = _pair2d(40, k)
     u0 = O.project(p, O.IC_QUADRANT2D, I.quadrant_params(3))
