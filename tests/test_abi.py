@@ -72,6 +72,24 @@ def test_pure_calls_without_gpu(lib):
     bad = N.Mesh(2, 0, 5, 0.0, 1.0, 0.0, 1.0, (ctypes.c_int * 4)(1, 1, 1, 1))
     assert L.dg_workspace_size(ctypes.byref(bad), 2, N.EQ_EULER, ctypes.byref(p), ctypes.byref(n)) == -1
     assert L.dg_workspace_size(ctypes.byref(mesh), 5, N.EQ_EULER, ctypes.byref(p), ctypes.byref(n)) == -8
+    # more than 2^31 cells: unsupported (the size is refused before anything is allocated)
+    huge = N.Mesh(2, 65536, 32769, 0.0, 1.0, 0.0, 1.0, (ctypes.c_int * 4)(1, 1, 1, 1))
+    assert L.dg_workspace_size(ctypes.byref(huge), 1, N.EQ_EULER, ctypes.byref(p), ctypes.byref(n)) == -8
+    # one periodic and one outflow side on the same axis: invalid
+    half = N.Mesh(1, 64, 1, 0.0, 1.0, 0.0, 1.0, (ctypes.c_int * 4)(0, 1, 0, 0))
+    assert L.dg_workspace_size(ctypes.byref(half), 2, N.EQ_BURGERS, ctypes.byref(p), ctypes.byref(n)) == -1
+    # the hybrid limiter needs the filter on and excludes the positivity limiter
+    q = N.Params()
+    L.dg_params_default(ctypes.byref(q))
+    q.hybrid, q.positivity = 1, 1
+    assert L.dg_workspace_size(ctypes.byref(mesh), 2, N.EQ_EULER, ctypes.byref(q), ctypes.byref(n)) == -8
+    q.positivity, q.enabled = 0, 0
+    assert L.dg_workspace_size(ctypes.byref(mesh), 2, N.EQ_EULER, ctypes.byref(q), ctypes.byref(n)) == -8
+    q.enabled = 1
+    assert L.dg_workspace_size(ctypes.byref(mesh), 2, N.EQ_EULER, ctypes.byref(q), ctypes.byref(n)) == 0
+    # a non-positive CFL number or gamma <= 1: invalid
+    q.cfl = 0.0
+    assert L.dg_workspace_size(ctypes.byref(mesh), 2, N.EQ_EULER, ctypes.byref(q), ctypes.byref(n)) == -1
 
 
 def test_splitmix64_reference_stream():
