@@ -173,6 +173,35 @@ extern "C" dg_status dg_workspace_size(const dg_mesh* mesh, int degree, int equa
   return DG_OK;
 }
 
+// One warp per (strip, chunk) item, so a 2D stage launch runs in waves of the resident warps. A
+// warp sweeps H + 4 rows (two halo rows on each side): pick the H that minimises waves x (H + 4),
+// never below 8 rows (the halo would dominate).
+int dgk::default_chunk_rows(const StageLauncher& L, int nstrips, int ny, int wpb, unsigned block, size_t smem) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    nsm = 152;
+  int bps = L.blocks_per_sm ? L.blocks_per_sm(block, smem) : 0;
+  if (bps <= 0) bps = 1;
+  const long long W = (long long)nsm * bps * wpb;
+  long long best = -1;
+  int H = 8;
+  for (int w = 1; w <= 16; ++w) {
+    long long nch = w * W / nstrips;
+    if (nch < 1) nch = 1;
+    if (nch > ny) nch = ny;
+    int h = (int)((ny + nch - 1) / nch);
+    if (h < 8) h = 8;
+    const long long items = (long long)nstrips * ((ny + h - 1) / h);
+    const long long cost = ((items + W - 1) / W) * (h + 4);
+    if (best < 0 || cost < best) {
+      best = cost;
+      H = h;
+    }
+  }
+  return H;
+}
+
 static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (s->dim == 1) {
     s->L = stage1d_launcher(s->k, s->eq, s->prec);
@@ -190,29 +219,24 @@ static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (!s->L.launch) return DG_ERR_UNSUPPORTED;
   const int nx = s->mesh.nx, ny = s->mesh.ny;
   s->nstrips = (nx + STRIP_OUT - 1) / STRIP_OUT;
-  // rows per chunk: enough warps to fill the GPU about twice, never fewer than 8 rows
-  int H = tile_rows;
-  if (H <= 0) {
-    long long target = 152LL * 16;
-    H = (int)((long long)s->nstrips * ny / target);
-    if (H < 8) H = 8;
-    if (H > 256) H = 256;
-  }
-  if (H > ny) H = ny;
-  s->H = H;
-  s->nchunks = (ny + H - 1) / H;
-  // warps per block limited by shared memory (row slots)
+  // warps per block: 4 by default (the kernels hold about 255 registers a thread, so an SM keeps
+  // 8 warps either way and smaller blocks fill it in finer steps), limited by the row slots
   size_t per_warp = s->L.slot_bytes_per_warp;
   int wpb = (int)((200 * 1024 - 256) / per_warp);
   if (wpb > 8) wpb = 8;
-  if (tile_warps > 0 && tile_warps < wpb) wpb = tile_warps;
+  const int want = tile_warps > 0 ? tile_warps : 4;
+  if (want < wpb) wpb = want;
   if (wpb < 1) return DG_ERR_UNSUPPORTED;
   s->warps_per_block = wpb;
   s->block = 32 * wpb;
-  long long nw = (long long)s->nstrips * s->nchunks;
-  s->grid = (unsigned)((nw + wpb - 1) / wpb);
   s->smem = 256 + per_warp * wpb;
   CK(s->L.set_smem(s->smem));
+  int H = tile_rows > 0 ? tile_rows : default_chunk_rows(s->L, s->nstrips, ny, wpb, s->block, s->smem);
+  if (H > ny) H = ny;
+  s->H = H;
+  s->nchunks = (ny + H - 1) / H;
+  long long nw = (long long)s->nstrips * s->nchunks;
+  s->grid = (unsigned)((nw + wpb - 1) / wpb);
   return DG_OK;
 }
 

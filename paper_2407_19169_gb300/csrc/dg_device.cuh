@@ -381,6 +381,68 @@ __host__ __device__ inline df df_from_double(double x) {
   return {hi, lo};
 }
 
+// ---- two FP32 lanes in one register pair (the packed FP32 instructions of sm_100 and later) ----
+// Each lane is rounded to nearest exactly like the scalar instruction, so a sum of products
+// formed lane-wise with vmad equals the scalar FMA chain bit for bit (the sign of a zero sum
+// aside: packed sums start at +0, scalar ones at -0).
+struct f2 {
+  float x, y;
+};
+__device__ __forceinline__ float2 f2v(f2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ f2 f2of(float2 a) { return f2{a.x, a.y}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2of(__fadd2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+  f2 d;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ f2 operator-(f2 a) { return f2{-a.x, -a.y}; }
+
+// value-type generic arithmetic for the sum-factorised kernels: T = float, double or f2
+template <class V>
+struct vtraits {
+  using S = V;
+  static __device__ __forceinline__ V zero() { return V(-0.0); }   // additive identity
+};
+template <>
+struct vtraits<f2> {
+  using S = float;
+  static __device__ __forceinline__ f2 zero() { return f2{0.f, 0.f}; }
+};
+__device__ __forceinline__ float vmad(float x, float c, float acc) { return acc + x * c; }
+__device__ __forceinline__ double vmad(double x, double c, double acc) { return acc + x * c; }
+__device__ __forceinline__ f2 vmad(f2 x, float c, f2 acc) {
+  return f2of(__ffma2_rn(f2v(x), make_float2(c, c), f2v(acc)));
+}
+__device__ __forceinline__ float vscale(float x, float c) { return x * c; }
+__device__ __forceinline__ double vscale(double x, double c) { return x * c; }
+__device__ __forceinline__ f2 vscale(f2 x, float c) { return f2of(__fmul2_rn(f2v(x), make_float2(c, c))); }
+// A sum whose first term is taken as it is (no add to a zero): in the fully unrolled callers the
+// flag is a compile-time constant at every use.
+template <class V>
+struct vsum {
+  V s;
+  bool any = false;
+  __device__ __forceinline__ void add(V x) {
+    s = any ? s + x : x;
+    any = true;
+  }
+  __device__ __forceinline__ V get() const { return any ? s : vtraits<V>::zero(); }
+};
+__device__ __forceinline__ float shfl_down_v(float x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
+__device__ __forceinline__ double shfl_down_v(double x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
+__device__ __forceinline__ f2 shfl_down_v(f2 x, int d) {
+  return f2{__shfl_down_sync(0xffffffffu, x.x, d), __shfl_down_sync(0xffffffffu, x.y, d)};
+}
+__device__ __forceinline__ float shfl_up_v(float x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
+__device__ __forceinline__ double shfl_up_v(double x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
+__device__ __forceinline__ f2 shfl_up_v(f2 x, int d) {
+  return f2{__shfl_up_sync(0xffffffffu, x.x, d), __shfl_up_sync(0xffffffffu, x.y, d)};
+}
+
 // Atomic max of a non-negative double through its bit pattern (monotone for x >= 0; NaN sorts
 // above +inf, so a NaN rate is kept and reported).
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double x) {

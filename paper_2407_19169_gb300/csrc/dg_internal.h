@@ -15,7 +15,13 @@ struct StageLauncher {
   cudaError_t (*launch)(const void* args, unsigned grid, unsigned block, size_t smem, cudaStream_t s);
   cudaError_t (*set_smem)(size_t bytes);  // raise the dynamic shared-memory limit
   size_t slot_bytes_per_warp;             // 2D: per-warp row slots; 1D: 0
+  // resident blocks per SM for a block size and dynamic shared memory (2D; 0 if unknown)
+  int (*blocks_per_sm)(unsigned block, size_t smem);
 };
+
+// Rows per chunk of the 2D stage kernel when the caller gives none: the fewest waves of resident
+// warps times the rows a warp sweeps (H + 4 halo rows). Queries the current device.
+int default_chunk_rows(const StageLauncher& L, int nstrips, int ny, int wpb, unsigned block, size_t smem);
 
 // Instantiation tables (one per kernel file). Return {nullptr} if the combination is not compiled.
 StageLauncher stage1d_launcher(int K, int EQ, int PREC);

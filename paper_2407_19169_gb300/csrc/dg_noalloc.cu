@@ -150,16 +150,14 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
     StageLauncher L = stage2d_f64_launcher(k, eq, basis);
     if (!L.launch) return DG_ERR_UNSUPPORTED;
     const int nstrips = (m->nx + STRIP_OUT - 1) / STRIP_OUT;
-    int H = (int)((long long)nstrips * m->ny / (152LL * 16));
-    if (H < 8) H = 8;
-    if (H > 256) H = 256;
-    if (H > m->ny) H = m->ny;
-    const int nchunks = (m->ny + H - 1) / H;
     int wpb = (int)((200 * 1024 - 256) / L.slot_bytes_per_warp);
-    if (wpb > 8) wpb = 8;
+    if (wpb > 4) wpb = 4;
     if (wpb < 1) return DG_ERR_UNSUPPORTED;
     const size_t smem = 256 + L.slot_bytes_per_warp * wpb;
     if (L.set_smem(smem) != cudaSuccess) return DG_ERR_CUDA;
+    int H = default_chunk_rows(L, nstrips, m->ny, wpb, 32u * wpb, smem);
+    if (H > m->ny) H = m->ny;
+    const int nchunks = (m->ny + H - 1) / H;
     const long long nw = (long long)nstrips * nchunks;
     for (int s = 0; s < 3; ++s) {
       Stage2DArgs a;

@@ -16,9 +16,17 @@ static cudaError_t smem2d(size_t bytes) {
                               (int)bytes);
 }
 template <int K, int EQ, int B>
+static int occ2d(unsigned block, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage2d_kernel<K, EQ, B, PrecF64>, (int)block, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+template <int K, int EQ, int B>
 static StageLauncher make2d() {
   return StageLauncher{&launch2d<K, EQ, B>, &smem2d<K, EQ, B>,
-                       Stage2D<K, EQ, B, PrecF64>::slot_bytes_per_warp()};
+                       Stage2D<K, EQ, B, PrecF64>::slot_bytes_per_warp(), &occ2d<K, EQ, B>};
 }
 
 template <int K, int B>
