@@ -440,13 +440,16 @@ def main():
     # ---- the plain FP64 path ----
     fp64 = None
     if not args.skip_fp64:
-        s64 = make_solver(N, N.PREC_FP64, nx, seed, sh, tile)
+        # the library's default schedule: the FP32 tile does not carry over (the FP64 kernel's row
+        # slots are twice as large, so fewer of its blocks fit in shared memory)
+        s64 = make_solver(N, N.PREC_FP64, nx, seed, sh)
         s64.advance_steps(args.warmup)
         torch.cuda.synchronize()
         k64 = args.fp64_steps
         ms64, launches64 = time_steps(torch, s64, k64, stream, barrier)
         fp64 = {"value": 3.0 * ndof * k64 / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
                 "ms_per_step": ms64 / k64, "stage_kernel_ms": ms64 / (3 * k64), "dtype": "f64",
+                "tile": "library default",
                 "hbm_frac": (8.0 / 3.0) * 8 * ndof / (ms64 / (3 * k64) * 1e-3) / 1e9 / peaks()[0]}
         s64.close()
         del s64

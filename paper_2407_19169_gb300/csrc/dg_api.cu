@@ -202,6 +202,23 @@ int dgk::default_chunk_rows(const StageLauncher& L, int nstrips, int ny, int wpb
   return H;
 }
 
+// Warps per block when the caller gives none: of 4, 2, 8 and 1 warps (within max_wpb, the row-slot
+// limit), the block with the most resident warps per SM; ties keep the earlier candidate.
+int dgk::default_block_warps(const StageLauncher& L, int max_wpb) {
+  int best = -1, wpb = max_wpb < 4 ? max_wpb : 4;
+  for (int c : {4, 2, 8, 1}) {
+    if (c > max_wpb) continue;
+    const size_t smem = 256 + L.slot_bytes_per_warp * c;
+    if (L.set_smem(smem) != cudaSuccess) continue;
+    const int bps = L.blocks_per_sm ? L.blocks_per_sm(32u * c, smem) : 0;
+    if (bps * c > best) {
+      best = bps * c;
+      wpb = c;
+    }
+  }
+  return wpb;
+}
+
 static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (s->dim == 1) {
     s->L = stage1d_launcher(s->k, s->eq, s->prec);
@@ -219,14 +236,17 @@ static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (!s->L.launch) return DG_ERR_UNSUPPORTED;
   const int nx = s->mesh.nx, ny = s->mesh.ny;
   s->nstrips = (nx + STRIP_OUT - 1) / STRIP_OUT;
-  // warps per block: 4 by default (the kernels hold about 255 registers a thread, so an SM keeps
-  // 8 warps either way and smaller blocks fill it in finer steps), limited by the row slots
+  // warps per block: the caller's, else the block size with the most resident warps; at most the
+  // row slots that fit in 200 KB of shared memory
   size_t per_warp = s->L.slot_bytes_per_warp;
   int wpb = (int)((200 * 1024 - 256) / per_warp);
   if (wpb > 8) wpb = 8;
-  const int want = tile_warps > 0 ? tile_warps : 4;
-  if (want < wpb) wpb = want;
   if (wpb < 1) return DG_ERR_UNSUPPORTED;
+  if (tile_warps > 0) {
+    if (tile_warps < wpb) wpb = tile_warps;
+  } else {
+    wpb = default_block_warps(s->L, wpb);
+  }
   s->warps_per_block = wpb;
   s->block = 32 * wpb;
   s->smem = 256 + per_warp * wpb;

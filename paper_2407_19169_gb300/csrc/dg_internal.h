@@ -22,6 +22,9 @@ struct StageLauncher {
 // Rows per chunk of the 2D stage kernel when the caller gives none: the fewest waves of resident
 // warps times the rows a warp sweeps (H + 4 halo rows). Queries the current device.
 int default_chunk_rows(const StageLauncher& L, int nstrips, int ny, int wpb, unsigned block, size_t smem);
+// Warps per block of the 2D stage kernel when the caller gives none: the most resident warps per SM
+// (4, 2, 8 or 1 warps, at most max_wpb). Changes the kernel's dynamic shared-memory limit.
+int default_block_warps(const StageLauncher& L, int max_wpb);
 
 // Instantiation tables (one per kernel file). Return {nullptr} if the combination is not compiled.
 StageLauncher stage1d_launcher(int K, int EQ, int PREC);

@@ -151,8 +151,9 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
     if (!L.launch) return DG_ERR_UNSUPPORTED;
     const int nstrips = (m->nx + STRIP_OUT - 1) / STRIP_OUT;
     int wpb = (int)((200 * 1024 - 256) / L.slot_bytes_per_warp);
-    if (wpb > 4) wpb = 4;
+    if (wpb > 8) wpb = 8;
     if (wpb < 1) return DG_ERR_UNSUPPORTED;
+    wpb = default_block_warps(L, wpb);
     const size_t smem = 256 + L.slot_bytes_per_warp * wpb;
     if (L.set_smem(smem) != cudaSuccess) return DG_ERR_CUDA;
     int H = default_chunk_rows(L, nstrips, m->ny, wpb, 32u * wpb, smem);
