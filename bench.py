@@ -258,17 +258,22 @@ def run_small_configs(torch, N, stream, barrier):
     return out
 
 
-def run_served(N, stream, rate, n_req, budget, policy="srpt"):
-    """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching."""
+def run_served(N, stream, rate, n_req, budget, policy="srpt", precision=None, sides=None):
+    """S3: a Poisson stream of 2D Euler Q2 quadrant solves served with continuous batching (FP32
+    form; precision=PREC_FP64 serves the plain FP64 path, each solve stepped on its own)."""
     from paper_2407_19169_gb300 import serve as S
-    reqs = S.poisson_requests(rate=rate, n=n_req, seed=5, seeds=accepted("quadrant_seeds.txt"))
-    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream, positivity=1, policy=policy)
+    precision = N.PREC_FP32_MIXED if precision is None else precision
+    reqs = S.poisson_requests(rate=rate, n=n_req, seed=5, seeds=accepted("quadrant_seeds.txt"),
+                              sides=sides or S.SIDES)
+    eng = S.Engine(budget_bytes=budget, chunk_steps=16, stream=stream.cuda_stream, positivity=1, policy=policy,
+                   precision=precision)
     t0 = time.perf_counter()
     results, stats = eng.run(reqs)
     wall = time.perf_counter() - t0
     out = S.summarize(results, wall)
     out.update({"rate_per_s": rate, "requests": n_req, "budget_gb": budget / 1e9, **stats,
-                "sides": sorted({r.side for r in reqs}), "precision": "FP32 form", "positivity_limiter": True,
+                "sides": sorted({r.side for r in reqs}),
+                "precision": "FP64" if precision == N.PREC_FP64 else "FP32 form", "positivity_limiter": True,
                 "policy": policy})
     return out
 

@@ -6,6 +6,9 @@ them with dg_batch_run in chunks of a few steps; at every chunk boundary it reti
 reached their end time (each stops exactly at its own T) and admits waiting requests while the
 device-memory budget allows. Latency = completion time - arrival time.
 
+In the FP32 form a round is one dg_batch_run over the chosen solves; the plain FP64 path (no
+batched kernel) advances each chosen solve with its own dg_advance_steps.
+
 Which resident solves a round advances is the scheduling policy: "all" advances every one; "srpt"
 (shortest remaining work first) advances the solves with the least estimated remaining work,
 (T - t) * side^3 (steps grow with side / CFL, cells with side^2), adding them until they cover
@@ -127,7 +130,14 @@ class Engine:
                 pick = pick_round(rem, [req.side * req.side for req, s, adm, need in active], self.fill_cells)
             else:
                 pick = list(range(len(active)))
-            st = N.batch_run([active[i][1] for i in pick], self.chunk)
+            chosen = [active[i][1] for i in pick]
+            if self.precision == N.PREC_FP64:
+                # the plain FP64 path: batched stepping is FP32-form only, so each solve advances
+                # on its own (its steps queue on the shared stream, the solves still resident)
+                for s in chosen:
+                    s.advance_steps(self.chunk)
+            else:
+                N.batch_run(chosen, self.chunk)
             still = []
             for idx, (req, s, adm, need) in enumerate(active):
                 if idx not in pick:
@@ -148,7 +158,6 @@ class Engine:
                 else:
                     still.append((req, s, adm, need))
             active = still
-            del st
         return results, {"peak_active": peak_active, "peak_bytes": peak_bytes}
 
 

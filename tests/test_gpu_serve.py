@@ -31,3 +31,20 @@ def test_served_results_equal_alone_under_budget():
         assert np.abs(r.state - ua).sum() <= 1e-12 * np.abs(ua).sum()
     summary = S.summarize(results, max(r.done for r in results))
     assert summary["completed"] == 8 and summary["p99_s"] >= summary["p50_s"] > 0
+
+
+def test_served_fp64_results_equal_alone():
+    # the plain FP64 path steps each resident solve on its own: results equal solo runs bitwise
+    reqs = S.poisson_requests(rate=400.0, n=4, seed=6, seeds=SEEDS, sides=(32, 48), t_range=(0.01, 0.03))
+    eng = S.Engine(budget_bytes=1e9, chunk_steps=8, keep_states=True, positivity=1, precision=N.PREC_FP64)
+    results, stats = eng.run(reqs)
+    assert len(results) == len(reqs) and all(r.status == 0 for r in results)
+    for r in results:
+        req = reqs[r.rid]
+        alone = N.Solver(dim=2, nx=req.side, ny=req.side, bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER,
+                         precision=N.PREC_FP64, positivity=1)
+        alone.set_initial(N.IC_QUADRANT2D, I.quadrant_params(req.seed))
+        alone.advance_to(req.T)
+        ua, ta = alone.read_state()
+        assert ta == req.T
+        np.testing.assert_array_equal(r.state, ua)
