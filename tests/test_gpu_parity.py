@@ -140,7 +140,7 @@ def test_euler_2d_tiny_and_thin_meshes(nx, ny, bc):
     assert rel_l1(p, ug, uo) <= TOL
 
 
-@pytest.mark.parametrize("nx", [1, 2, 28, 29, 57])
+@pytest.mark.parametrize("nx", [1, 2, 28, 29, 57, 448, 449])
 def test_burgers_1d_tiny_and_seams(nx):
     p, s = pair(dim=1, nx=nx, x0=0, x1=nx * 0.1, k=2, eq="burgers", bc="periodic")
     u0 = I.random_modal_state(p.shape, 60 + nx, [(0.2, 1.2)])
