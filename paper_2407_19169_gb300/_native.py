@@ -212,6 +212,12 @@ class Solver:
         check(st, "dg_advance_to")
         return n.value
 
+    def advance_toward(self, T: float, max_steps: int) -> int:
+        """dg_advance_to with at most max_steps steps; returns its status without raising
+        (DG_ERR_TIMEOUT = stopped at max_steps before T; dg_sync reports the solve's state)."""
+        n = C.c_longlong()
+        return load().dg_advance_to(self.handle, T, max_steps, C.byref(n))
+
     def advance_steps(self, n: int) -> None:
         check(load().dg_advance_steps(self.handle, n), "dg_advance_steps")
 

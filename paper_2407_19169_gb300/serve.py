@@ -7,7 +7,7 @@ reached their end time (each stops exactly at its own T) and admits waiting requ
 device-memory budget allows. Latency = completion time - arrival time.
 
 In the FP32 form a round is one dg_batch_run over the chosen solves; the plain FP64 path (no
-batched kernel) advances each chosen solve with its own dg_advance_steps.
+batched kernel) advances each chosen solve on its own with dg_advance_to, at most a chunk of steps.
 
 Which resident solves a round advances is the scheduling policy: "all" advances every one; "srpt"
 (shortest remaining work first) advances the solves with the least estimated remaining work,
@@ -130,14 +130,13 @@ class Engine:
                 pick = pick_round(rem, [req.side * req.side for req, s, adm, need in active], self.fill_cells)
             else:
                 pick = list(range(len(active)))
-            chosen = [active[i][1] for i in pick]
             if self.precision == N.PREC_FP64:
                 # the plain FP64 path: batched stepping is FP32-form only, so each solve advances
-                # on its own (its steps queue on the shared stream, the solves still resident)
-                for s in chosen:
-                    s.advance_steps(self.chunk)
+                # on its own, up to chunk steps toward its end time (the solves stay resident)
+                for i in pick:
+                    active[i][1].advance_toward(active[i][0].T, self.chunk)
             else:
-                N.batch_run(chosen, self.chunk)
+                N.batch_run([active[i][1] for i in pick], self.chunk)
             still = []
             for idx, (req, s, adm, need) in enumerate(active):
                 if idx not in pick:
