@@ -1118,6 +1118,36 @@ struct Stage2D {
     if (a.hybrid) hybrid_max(a.hyb, my_eta);
   }
 
+  // All variables of a cell at limiter point i, w[v] = sum_m coef(i, m) uo[v][m] (the coefficients
+  // fold to immediates in the unrolled callers); pairs of variables in packed FP32 (PACK).
+  template <class CF>
+  static __device__ __forceinline__ void point_w(const T (&uo)[NV][NM], int i, const CF& coef, T (&w)[NV]) {
+    if constexpr (PACK) {
+#pragma unroll
+      for (int vp = 0; vp < NV / 2; ++vp) {
+        f2 x{0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const double c = coef(i, m);
+          if (c != 0.0) x = vmad(f2{uo[2 * vp][m], uo[2 * vp + 1][m]}, (T)c, x);
+        }
+        w[2 * vp] = x.x;
+        w[2 * vp + 1] = x.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T x = T(0);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const double c = coef(i, m);
+          if (c != 0.0) x += (T)c * uo[v][m];
+        }
+        w[v] = x;
+      }
+    }
+  }
+
   // Max CFL rate beta^x / hx + beta^y / hy over the positivity limiter's points of one cell: with
   // the limiter on, Zhang and Shu's positivity result for the averages needs the CFL bound on the
   // wave speeds at those points, not only at the average.
@@ -1129,21 +1159,14 @@ struct Stage2D {
       constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
       constexpr int NP = NQ * NQ + 4 * NQ;
       const T thx = (T)hx, thy = (T)hy;
+      auto coef = [&](int i, int m) -> double {
+        return i < NQ * NQ ? VE[i * NM + m]
+                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
+      };
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T w[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T x = T(0);
-#pragma unroll
-          for (int m = 0; m < NM; ++m) {
-            const double c = i < NQ * NQ ? VE[i * NM + m]
-                                         : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m]
-                                                                 : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
-            if (c != 0.0) x += (T)c * uo[v][m];
-          }
-          w[v] = x;
-        }
+        point_w(uo, i, coef, w);
         T bx, by, invH;
         bool ph;
         avg_params<EQ, 2>(w, gam, gm1, T(0), T(0), bx, by, invH, ph);
@@ -1200,16 +1223,7 @@ struct Stage2D {
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T w[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T x = T(0);
-#pragma unroll
-          for (int m = 0; m < NM; ++m) {
-            const double c = coef(i, m);
-            if (c != 0.0) x += (T)c * uo[v][m];
-          }
-          w[v] = x;
-        }
+        point_w(uo, i, coef, w);
         if (pressure_of<NV>(w, gm1) < eps) {
           const T t = pp_segment<NV>(ub, w, eps, gm1);
           th2 = t < th2 ? t : th2;
@@ -1271,16 +1285,7 @@ struct Stage2D {
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T w[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T x = T(0);
-#pragma unroll
-          for (int m = 0; m < NM; ++m) {
-            const double c = coef(i, m);
-            if (c != 0.0) x += (T)c * uo[v][m];
-          }
-          w[v] = x;
-        }
+        point_w(uo, i, coef, w);
         if (pressure_of<NV>(w, gm1) < eps) {
           const T t = pp_segment<NV>(ub, w, eps, gm1);
           th2 = t < th2 ? t : th2;
