@@ -401,6 +401,52 @@ __device__ __forceinline__ f2 operator-(f2 a, f2 b) {
 }
 __device__ __forceinline__ f2 operator-(f2 a) { return f2{-a.x, -a.y}; }
 
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2of(__fmul2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2of(__ffma2_rn(f2v(a), f2v(b), f2v(c))); }
+
+// Two double-float values (two variables) in register pairs; every lane performs exactly the
+// operations of the scalar df functions and df_acc below, so the results are bitwise the same.
+struct df2 {
+  f2 hi, lo;
+};
+__device__ __forceinline__ df2 df2_fast_two_sum(f2 a, f2 b) {
+  const f2 s = a + b;
+  return {s, b - (s - a)};
+}
+// a (one double-float for both lanes) times b
+__device__ __forceinline__ df2 df2_mul(df a, df2 b) {
+  const f2 ah{a.hi, a.hi}, al{a.lo, a.lo};
+  const f2 p = ah * b.hi;
+  f2 e = vfma(ah, b.hi, -p);
+  e = vfma(ah, b.lo, e);
+  e = vfma(al, b.hi, e);
+  return df2_fast_two_sum(p, e);
+}
+struct df2_acc {
+  f2 hi, lo;
+  __device__ __forceinline__ void add(f2 x) {
+    const f2 s = hi + x;
+    const f2 bb = s - hi;
+    const f2 e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo = lo + e;
+  }
+  __device__ __forceinline__ void add(df2 x) {
+    add(x.hi);
+    lo = lo + x.lo;
+  }
+  // + a * b: a.hi * b exactly as p + e (FMA), a.lo * b rounded
+  __device__ __forceinline__ void add_prod(df a, f2 b) {
+    const f2 ah{a.hi, a.hi}, al{a.lo, a.lo};
+    const f2 p = ah * b;
+    f2 e = vfma(ah, b, -p);
+    e = vfma(al, b, e);
+    add(p);
+    lo = lo + e;
+  }
+  __device__ __forceinline__ df2 result() const { return df2_fast_two_sum(hi, lo); }
+};
+
 // value-type generic arithmetic for the sum-factorised kernels: T = float, double or f2
 template <class V>
 struct vtraits {

@@ -124,6 +124,9 @@ struct Stage2D {
   // packed adds save (measured on GB300, Q2 2048^2: 0.947 ms per stage launch against 1.005 ms).
   static constexpr bool PACK = PR::MIXED && (NV % 2) == 0;
   static constexpr bool PACK_TRACES = PACK && K == 1;
+  // The double-float cell averages run packed at degree 3 only (1024^2: Q3 0.851 -> 0.820 ms; Q2
+  // unchanged; Q1 0.155 -> 0.166 ms, its register count fell from 160 to 128 and the schedule with it).
+  static constexpr bool PACK_DF = PACK && K >= 3;
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
   using TB = Tab2D<K, BASIS>;
@@ -684,7 +687,7 @@ struct Stage2D {
               const int s = slot_of(t - 1);
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
-                if constexpr (PR::MIXED) {
+                if constexpr (PR::MIXED && !PACK_DF) {
                   df_acc acc0{*slot_ptr(ws, s, v, 0, lane), *slot_ptr(ws, s, v, NM, lane)};
                   acc0.add_prod(dfy, -Mh[v][0]);
                   const df r0 = acc0.result();
@@ -704,6 +707,19 @@ struct Stage2D {
 #pragma unroll
                 for (int vp = 0; vp < NV / 2; ++vp) {
                   const int v0 = 2 * vp, v1 = v0 + 1;
+                  if constexpr (PACK_DF) {
+                    T* h0 = slot_ptr(ws, s, v0, 0, lane);
+                    T* h1 = slot_ptr(ws, s, v1, 0, lane);
+                    T* l0 = slot_ptr(ws, s, v0, NM, lane);
+                    T* l1 = slot_ptr(ws, s, v1, NM, lane);
+                    df2_acc acc0{f2{*h0, *h1}, f2{*l0, *l1}};
+                    acc0.add_prod(dfy, -f2{Mh[v0][0], Mh[v1][0]});
+                    const df2 r0 = acc0.result();
+                    *h0 = r0.hi.x;
+                    *h1 = r0.hi.y;
+                    *l0 = r0.lo.x;
+                    *l1 = r0.lo.y;
+                  }
                   f2 ms[K + 1];
 #pragma unroll
                   for (int p = 0; p <= K; ++p) ms[p] = vscale(f2{Mh[v0][p], Mh[v1][p]}, sy);
@@ -821,7 +837,7 @@ struct Stage2D {
           if (a.stage > 0) ST::load(a.un, a.ncell, cell, un_, unlo);
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            if constexpr (PR::MIXED) {
+            if constexpr (PR::MIXED && !PACK_DF) {
               // cell average in double-float from the edge integrals, each formed once per edge:
               // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B [- Phi_T at the next row])
               df_acc m0{u[v][0], lo0[v]};
@@ -853,6 +869,24 @@ struct Stage2D {
 #pragma unroll
             for (int vp = 0; vp < NV / 2; ++vp) {
               const int v0 = 2 * vp, v1 = v0 + 1;
+              if constexpr (PACK_DF) {
+                // the double-float cell averages of the scalar branch, two variables per pair
+                const f2 uh{u[v0][0], u[v1][0]}, ul{lo0[v0], lo0[v1]};
+                df2_acc m0{uh, ul};
+                if (a.stage > 0) {
+                  df2_acc d{f2{un_[v0][0], un_[v1][0]}, f2{unlo[v0], unlo[v1]}};
+                  d.add(df2{-uh, -ul});
+                  m0.add(df2_mul(dfc0, d.result()));
+                }
+                m0.add_prod(dfx, f2{ML[v0][0], ML[v1][0]});
+                m0.add_prod(dfx, -f2{MR[v0][0], MR[v1][0]});
+                m0.add_prod(dfy, f2{Mh[v0][0], Mh[v1][0]});
+                const df2 r0 = m0.result();
+                *slot_ptr(ws, s, v0, 0, lane) = r0.hi.x;
+                *slot_ptr(ws, s, v1, 0, lane) = r0.hi.y;
+                *slot_ptr(ws, s, v0, NM, lane) = r0.lo.x;
+                *slot_ptr(ws, s, v1, NM, lane) = r0.lo.y;
+              }
 #pragma unroll
               for (int m = 1; m < NM; ++m) {
                 f2 val{u[v0][m], u[v1][m]};
