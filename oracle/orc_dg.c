@@ -469,15 +469,23 @@ void orc_hybrid(const orc_problem* p, const double* u, double dt, double* out) {
 /* ------------------------------------------------------------------------------------------ */
 /* Positivity-preserving limiter of Zhang and Shu (J. Comput. Phys. 229, 2010), applied after the */
 /* jump filter when the problem asks for it (the paper does so in Section 3.2).                   */
-/* Checked at every point where the scheme evaluates the cell polynomial: the volume Gauss points */
-/* and the Gauss points of the edges (1D: Gauss points and both ends).                           */
+/* Checked at every point where the scheme evaluates the cell polynomial, the volume Gauss points */
+/* and the Gauss points of the edges (1D: Gauss points and both ends), and at the rest of Zhang   */
+/* and Shu's set: their positivity of the next averages rests on writing the average as a convex  */
+/* combination of values at the tensor points of the Gauss rule and the N-point Gauss-Lobatto     */
+/* rule with 2N - 3 >= k. For k = 2, 3 that is N = 3, whose interior node 0 adds the lines        */
+/* xi = 0 and eta = 0 crossed with the Gauss nodes (1D: the point 0); for k = 2 they are volume   */
+/* Gauss points already (0 is a node of the 3-point Gauss rule), for k = 3 they are new.         */
 /* ------------------------------------------------------------------------------------------ */
+#define ORC_MAXPP (ORC_MAXQ * ORC_MAXQ + 6 * ORC_MAXQ)
 static int pp_points(const orc_problem* p, const ctx_t* c, double* xi, double* eta) {
   int n = 0;
+  const int mid = p->k >= 2 && (c->nq % 2) == 0;   /* the Lobatto node 0 is not a Gauss node */
   if (p->dim == 1) {
     for (int a = 0; a < c->nq; ++a) { xi[n] = c->xq[a]; eta[n++] = 0.0; }
     xi[n] = -1.0; eta[n++] = 0.0;
     xi[n] = 1.0; eta[n++] = 0.0;
+    if (mid) { xi[n] = 0.0; eta[n++] = 0.0; }
     return n;
   }
   for (int a = 0; a < c->nq; ++a)
@@ -488,11 +496,16 @@ static int pp_points(const orc_problem* p, const ctx_t* c, double* xi, double* e
     xi[n] = c->xq[g]; eta[n++] = -1.0;
     xi[n] = c->xq[g]; eta[n++] = 1.0;
   }
+  if (mid)
+    for (int g = 0; g < c->nq; ++g) {
+      xi[n] = 0.0; eta[n++] = c->xq[g];
+      xi[n] = c->xq[g]; eta[n++] = 0.0;
+    }
   return n;
 }
 
 static void pp_cell(const orc_problem* p, const ctx_t* c, double* u, long cell) {
-  double xi[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ], eta[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ];
+  double xi[ORC_MAXPP], eta[ORC_MAXPP];
   const int np = pp_points(p, c, xi, eta);
   double ubar[ORC_MAXNV];
   for (int v = 0; v < c->nv; ++v) ubar[v] = U(u, v, 0, cell);
@@ -607,7 +620,7 @@ double orc_max_rate(const orc_problem* p, const double* u) {
   ctx_t c;
   make_ctx(p, &c);
   double best = 0.0;
-  double xi[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ], eta[ORC_MAXQ * ORC_MAXQ + 4 * ORC_MAXQ];
+  double xi[ORC_MAXPP], eta[ORC_MAXPP];
   const int np = (p->positivity && p->eq == ORC_EQ_EULER) ? pp_points(p, &c, xi, eta) : 0;
   for (long cell = 0; cell < c.ncell; ++cell) {
     double ubar[ORC_MAXNV];

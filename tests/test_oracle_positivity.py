@@ -23,6 +23,28 @@ def test_density_scaling_closed_form():
     assert out[0, 0, 0] == u[0, 0, 0] and out[2, 0, 0] == u[2, 0, 0]
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_lobatto_midline_points_closed_form(dim):
+    # k = 3: rho = 1 + 2.5 P_2(x) is -0.25 at x = 0 but positive at the 4 Gauss nodes (0.18 at
+    # +-0.34, 2.3 at +-0.86) and at the ends (3.5). Zhang and Shu's set takes the 3-point
+    # Gauss-Lobatto node 0 as well (2N - 3 >= k), so the limiter acts: theta_1 = (1 - eps) / 1.25.
+    if dim == 1:
+        p = O.Problem(dim=1, nx=1, x0=0.0, x1=0.1, k=3, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
+    else:
+        p = O.Problem(dim=2, nx=1, ny=1, x0=0.0, x1=0.1, y0=0.0, y1=0.1, k=3, eq=O.EQ_EULER,
+                      bc=(O.BC_PERIODIC,) * 4, positivity=1)
+    u = np.zeros(p.shape)
+    u[0, 0, 0] = 1.0
+    u[0, 2, 0] = 2.5                 # mode 2 = P_2(x) (P_0(y) in 2D)
+    u[-1, 0, 0] = 2.5                # E = 2.5 at rest: p = 1 everywhere
+    xs, _ = O.gauss(4)
+    assert min(1.0 + 2.5 * (1.5 * x * x - 0.5) for x in xs) > 0.0
+    out = O.positivity(p, u)
+    theta1 = (1.0 - 1e-10) / 1.25
+    assert out[0, 2, 0] == pytest.approx(2.5 * theta1, rel=1e-14)
+    assert O.evaluate(p, out, 0, 0.0, 0.3)[0] == pytest.approx(1e-10, abs=1e-14)
+
+
 def test_pressure_scaling_closed_form():
     p = one_cell(1)
     u = np.zeros(p.shape)
@@ -35,7 +57,7 @@ def test_pressure_scaling_closed_form():
     assert out[2, 1, 0] == pytest.approx(3.0 * theta2, rel=1e-12)
 
 
-@pytest.mark.parametrize("dim,k", [(1, 2), (1, 3), (2, 1), (2, 2)])
+@pytest.mark.parametrize("dim,k", [(1, 2), (1, 3), (2, 1), (2, 2), (2, 3)])
 def test_limited_state_is_admissible_and_conservative(dim, k):
     rng = np.random.default_rng(10 * dim + k)
     if dim == 1:
@@ -52,9 +74,14 @@ def test_limited_state_is_admissible_and_conservative(dim, k):
     np.testing.assert_array_equal(out[:, 0], u[:, 0])
     nq = k + 1
     xs, _ = O.gauss(nq)
-    pts = [(x, 0.0) for x in xs] + [(-1.0, 0.0), (1.0, 0.0)] if dim == 1 else \
-        [(a, b) for a in xs for b in xs] + [(s, x) for x in xs for s in (-1.0, 1.0)] + \
-        [(x, s) for x in xs for s in (-1.0, 1.0)]
+    # Zhang and Shu's set: Gauss nodes crossed with the N-point Gauss-Lobatto nodes, 2N - 3 >= k
+    # (N = 2: the ends; N = 3: the ends and 0), plus the volume Gauss points of the scheme
+    lob = [-1.0, 1.0] if 2 * 2 - 3 >= k else [-1.0, 0.0, 1.0]
+    if dim == 1:
+        pts = [(x, 0.0) for x in list(xs) + lob]
+    else:
+        pts = [(a, b) for a in xs for b in xs] + [(s, x) for x in xs for s in lob] + \
+            [(x, s) for x in xs for s in lob]
     for c in range(p.ncell):
         for (xi, eta) in pts:
             val = O.evaluate(p, out, c, xi, eta)
