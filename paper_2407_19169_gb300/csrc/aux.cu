@@ -176,13 +176,15 @@ __device__ inline double state_rate(const AuxGeom& g, const double* ub, bool& ph
 }
 
 // Max CFL rate over the cells' averages; with the positivity limiter also over its points (the
-// k+1 Gauss points per direction of the volume and the edges, 1D: Gauss points and both ends).
+// k+1 Gauss points per direction of the volume and the edges, 1D: Gauss points and both ends; for
+// k = 3 also the Gauss-Lobatto mid-lines xi = 0 and eta = 0 crossed with the Gauss nodes, 1D: 0).
 __global__ void rate_kernel(const AuxGeom g, const void* st, DevScalars* sc, int slot) {
   __shared__ double red[32];
   double r = 0.0;
   bool ok = true;
   const int nq = g.k + 1;
-  const int npt = !g.pp ? 0 : (g.dim == 1 ? nq + 2 : nq * nq + 4 * nq);
+  const int mid = (g.k >= 2 && nq % 2 == 0) ? 1 : 0;
+  const int npt = !g.pp ? 0 : (g.dim == 1 ? nq + 2 + mid : nq * nq + 4 * nq + 2 * nq * mid);
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double ub[4];
@@ -194,10 +196,14 @@ __global__ void rate_kernel(const AuxGeom g, const void* st, DevScalars* sc, int
     for (int i = 0; i < npt; ++i) {
       double xi, eta = 0.0;
       if (g.dim == 1) {
-        xi = i < nq ? c_gx[nq][i] : (i == nq ? -1.0 : 1.0);
+        xi = i < nq ? c_gx[nq][i] : (i == nq ? -1.0 : (i == nq + 1 ? 1.0 : 0.0));
       } else if (i < nq * nq) {
         xi = c_gx[nq][i / nq];
         eta = c_gx[nq][i % nq];
+      } else if (i >= nq * nq + 4 * nq) {
+        const int j = i - nq * nq - 4 * nq, gq = j >> 1;
+        xi = (j & 1) ? c_gx[nq][gq] : 0.0;
+        eta = (j & 1) ? 0.0 : c_gx[nq][gq];
       } else {
         const int e = (i - nq * nq) & 3, gq = (i - nq * nq) >> 2;
         xi = e == 0 ? -1.0 : (e == 1 ? 1.0 : c_gx[nq][gq]);

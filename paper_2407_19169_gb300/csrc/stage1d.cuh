@@ -285,14 +285,22 @@ struct Stage1D {
     if (a.hybrid) hybrid_max(a.hyb, my_eta);
   }
 
-  // Max CFL rate beta / h over the positivity limiter's points of one cell (Gauss points and both
-  // ends): with the limiter on, Zhang and Shu's positivity result for the averages needs the CFL
-  // bound on the wave speeds at those points.
-  static __device__ T point_rate(const T (&ut)[NV][NM], T gam, T gm1, double h) {
+  // The limiter's points: the Gauss points, both ends and, for k = 3, the node 0 of the 3-point
+  // Gauss-Lobatto rule (Zhang and Shu's positivity of the averages uses the Lobatto nodes with
+  // 2N - 3 >= k; for k = 2 the node 0 is a Gauss node already). Value of P_l at point i.
+  static constexpr int NP_LIM = NQ + 2 + ((K >= 2 && NQ % 2 == 0) ? 1 : 0);
+  static __device__ __forceinline__ double lim_coef(int i, int l) {
     constexpr carr<double, (K + 1) * NQ> GPT = TB::GP;
+    return i < NQ ? GPT[l * NQ + i] : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : (i == NQ + 1 ? 1.0 : GaussRule<1>::P(l, 0)));
+  }
+
+  // Max CFL rate beta / h over the positivity limiter's points of one cell: with the limiter on,
+  // Zhang and Shu's positivity result for the averages needs the CFL bound on the wave speeds at
+  // those points.
+  static __device__ T point_rate(const T (&ut)[NV][NM], T gam, T gm1, double h) {
     T best = T(0);
     if constexpr (EQ == EQ_EULER) {
-      constexpr int NP = NQ + 2;
+      constexpr int NP = NP_LIM;
       const T th = (T)h;
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
@@ -302,7 +310,7 @@ struct Stage1D {
           T x = T(0);
 #pragma unroll
           for (int l = 0; l < NM; ++l) {
-            const double c = i < NQ ? GPT[l * NQ + i] : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
+            const double c = lim_coef(i, l);
             x += (T)c * ut[v][l];
           }
           w[v] = x;
@@ -317,11 +325,10 @@ struct Stage1D {
   }
 
   // Zhang-Shu positivity-preserving limiter on one cell (after the filter, Section 3.2 of the
-  // paper), checked at the Gauss points and both ends; averages untouched.
+  // paper), checked at the limiter's points (lim_coef); averages untouched.
   static __device__ void positivity_limit(T (&ut)[NV][NM], T gm1) {
-    constexpr carr<double, (K + 1) * NQ> GPT = TB::GP;
     if constexpr (EQ == EQ_EULER) {
-      constexpr int NP = NQ + 2;
+      constexpr int NP = NP_LIM;
       T ub[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = ut[v][0];
@@ -336,9 +343,7 @@ struct Stage1D {
       eps = ub[0] < eps ? ub[0] : eps;
       eps = pbar < eps ? pbar : eps;
       if (!(eps > T(0)) || !(eps_r > T(0))) return;
-      auto coef = [&](int i, int l) -> double {
-        return i < NQ ? GPT[l * NQ + i] : (i == NQ ? ((l & 1) ? -1.0 : 1.0) : 1.0);
-      };
+      auto coef = [](int i, int l) -> double { return lim_coef(i, l); };
       T rmin = ub[0];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {

@@ -172,6 +172,34 @@ struct Stage2D {
     return t;
   }
 
+  // Zhang and Shu's Gauss-Lobatto mid-lines: their positivity of the averages uses the Gauss nodes
+  // crossed with the N-point Lobatto nodes, 2N - 3 >= k; for k = 3 (N = 3) the Lobatto node 0 is
+  // not a Gauss node, so the points (0, x_g) and (x_g, 0) are checked as well (P_l(0) is the
+  // 1-point Gauss rule's value table).
+  static constexpr int NMID = (K >= 2 && NQ % 2 == 0) ? 2 * NQ : 0;
+  __host__ __device__ static constexpr carr<double, (NMID > 0 ? NMID : 1) * NM> tab_mid() {
+    carr<double, (NMID > 0 ? NMID : 1) * NM> t{};
+    for (int g = 0; g < NQ && NMID > 0; ++g)
+      for (int m = 0; m < NM; ++m) {
+        t[(2 * g) * NM + m] = GaussRule<1>::P(MB::p(m), 0) * GR::P(MB::q(m), g);
+        t[(2 * g + 1) * NM + m] = GR::P(MB::p(m), g) * GaussRule<1>::P(MB::q(m), 0);
+      }
+    return t;
+  }
+  // the limiter's points: volume Gauss points, Gauss points of the edges, Lobatto mid-lines
+  static constexpr int NP_LIM = NQ * NQ + 4 * NQ + NMID;
+  // value of mode m at limiter point i (folds to an immediate for constant i, m)
+  static __device__ __forceinline__ double lim_coef(int i, int m) {
+    constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
+    constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
+    constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
+    constexpr carr<double, (NMID > 0 ? NMID : 1) * NM> TM = tab_mid();
+    return i < NQ * NQ ? VE[i * NM + m]
+                       : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m]
+                                               : (i < NQ * NQ + 4 * NQ ? TV[(i - NQ * NQ - 2 * NQ) * NM + m]
+                                                                       : TM[(i - NQ * NQ - 4 * NQ) * NM + m]));
+  }
+
   // row slot of row r (rows >= -2 occur; keep the index in 0..2)
   static __device__ __forceinline__ int slot_of(int r) { return ((r % 3) + 3) % 3; }
   static __device__ __forceinline__ T* slot_ptr(T* ws, int s, int v, int m, int lane) {
@@ -1188,15 +1216,9 @@ struct Stage2D {
   static __device__ T point_rate(const T (&uo)[NV][NM], T gam, T gm1, double hx, double hy) {
     T best = T(0);
     if constexpr (EQ == EQ_EULER) {
-      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
-      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
-      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
-      constexpr int NP = NQ * NQ + 4 * NQ;
+      constexpr int NP = NP_LIM;
       const T thx = (T)hx, thy = (T)hy;
-      auto coef = [&](int i, int m) -> double {
-        return i < NQ * NQ ? VE[i * NM + m]
-                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
-      };
+      auto coef = [](int i, int m) -> double { return lim_coef(i, m); };
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         T w[NV];
@@ -1215,10 +1237,7 @@ struct Stage2D {
   // points where the scheme evaluates the polynomial. Cell averages are not touched.
   static __device__ void positivity_limit(T (&uo)[NV][NM], T gm1) {
     if constexpr (EQ == EQ_EULER) {
-      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
-      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
-      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
-      constexpr int NP = NQ * NQ + 4 * NQ;
+      constexpr int NP = NP_LIM;
       T ub[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = uo[v][0];
@@ -1233,10 +1252,7 @@ struct Stage2D {
       eps = ub[0] < eps ? ub[0] : eps;
       eps = pbar < eps ? pbar : eps;
       if (!(eps > T(0)) || !(eps_r > T(0))) return;
-      auto coef = [&](int i, int m) -> double {
-        return i < NQ * NQ ? VE[i * NM + m]
-                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
-      };
+      auto coef = [](int i, int m) -> double { return lim_coef(i, m); };
       T rmin = ub[0];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
@@ -1279,10 +1295,7 @@ struct Stage2D {
     if constexpr (EQ != EQ_EULER) {
       return T(0);
     } else {
-      constexpr carr<double, NQ * NQ * NM> VE = tab_vol(0);
-      constexpr carr<double, 2 * NQ * NM> TH = tab_trace_h();
-      constexpr carr<double, 2 * NQ * NM> TV = tab_trace_v();
-      constexpr int NP = NQ * NQ + 4 * NQ;
+      constexpr int NP = NP_LIM;
       T ub[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = uo[v][0];
@@ -1295,10 +1308,7 @@ struct Stage2D {
       eps = pbar < eps ? pbar : eps;
       if (!(eps > T(0)) || !(eps_r > T(0))) return point_rate(uo, gam, gm1, hx, hy);
       const T thx = (T)hx, thy = (T)hy;
-      auto coef = [&](int i, int m) -> double {
-        return i < NQ * NQ ? VE[i * NM + m]
-                           : (i < NQ * NQ + 2 * NQ ? TH[(i - NQ * NQ) * NM + m] : TV[(i - NQ * NQ - 2 * NQ) * NM + m]);
-      };
+      auto coef = [](int i, int m) -> double { return lim_coef(i, m); };
       T rmin = ub[0];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {

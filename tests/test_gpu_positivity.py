@@ -47,6 +47,37 @@ def test_rough_1d_states_limiter_active(k):
     assert rel_l1(p, ug, uo) <= 1e-10
 
 
+@pytest.mark.parametrize("amp", [1.9, 2.5])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_lobatto_midline_points_match_oracle(dim, amp):
+    # k = 3 cells with rho = 1 + amp P_2(x) (plus a small seeded perturbation) at pressure 1: the
+    # density is lowest on the line x = 0, a Gauss-Lobatto mid-line point and not a Gauss point.
+    # amp = 1.9: admissible, the largest wave speed (the CFL rate) is there; amp = 2.5: negative
+    # there, limited by the oracle first, so rho(0) = 1e-10 and later stages limit again. A path
+    # without these points takes another dt and differs from the oracle.
+    n = 24
+    if dim == 1:
+        p = O.Problem(dim=1, nx=n, k=3, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
+        s = N.Solver(dim=1, nx=n, k=3, eq=N.EQ_EULER, bc=(N.BC_PERIODIC,) * 4, positivity=1)
+    else:
+        p = O.Problem(dim=2, nx=n, ny=n, k=3, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
+        s = N.Solver(dim=2, nx=n, ny=n, k=3, eq=N.EQ_EULER, bc=(N.BC_PERIODIC,) * 4, positivity=1,
+                     tile_rows=8)
+    rng = np.random.default_rng(30 + dim)
+    u0 = np.zeros(p.shape)
+    u0[0, 0] = 1.0 + 0.02 * rng.uniform(-1, 1, p.ncell)
+    u0[0, 2] = amp                                   # mode 2 = P_2(x) (P_0(y) in 2D)
+    u0[-1, 0] = 2.5 + 0.02 * rng.uniform(-1, 1, p.ncell)
+    u0 = O.positivity(p, u0)
+    assert (u0[0, 2] < amp).all() == (amp > 2.0)     # limited start only for amp = 2.5
+    s.write_state(u0)
+    s.advance_steps(3)
+    assert s.sync()[0] == 0
+    ug, _ = s.read_state()
+    uo, _, _ = O.advance(p, u0, 0.0, INF, 3)
+    assert rel_l1(p, ug, uo) <= 1e-10
+
+
 def test_fp32_form_survives_with_the_limiter():
     s = N.Solver(dim=2, nx=128, ny=128, k=2, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4,
                  precision=N.PREC_FP32_MIXED, positivity=1)
