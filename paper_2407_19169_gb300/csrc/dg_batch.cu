@@ -399,7 +399,7 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
         }
       }
       cls_wpb[c] = bw;
-      cls_cap[c] = (long long)nsm * bb;
+      cls_cap[c] = (long long)nsm * (bb > 0 ? bb : 1);
     }
     if (cls_count[c] > 0 && BL[c].set_smem) e = BL[c].set_smem(BL[c].warp_bytes * cls_wpb[c]);
   }
