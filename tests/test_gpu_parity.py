@@ -259,3 +259,30 @@ def test_full_size_2048_sampled(bc):
         ref = _window_step(p, u0, dt, ci, cj)
         got = ug[:, :, cj * nx + ci]
         np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("tile", [(128, 2), (128, 4), (0, 0)])
+def test_full_size_2048_sampled_fp32_form(tile):
+    """The FP32 form (the benchmark's path) at 2048 x 2048 Q2 Euler in the launch configurations the
+    benchmark uses (the autotuner's 128-row tiles, the default schedule), one step: sampled cells
+    against the oracle's windowed FP64 step within the FP32 form's 1e-5 bar (relative to each
+    cell's largest coefficient); the global dt within 1e-5 of the oracle's."""
+    nx = ny = 2048
+    p = O.Problem(dim=2, nx=nx, ny=ny, bc=(O.BC_OUTFLOW,) * 4, k=2, eq=O.EQ_EULER)
+    s = N.Solver(dim=2, nx=nx, ny=ny, bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER,
+                 precision=N.PREC_FP32_MIXED, tile_rows=tile[0], tile_warps=tile[1])
+    u0 = I.random_modal_state_fast(p.shape, 2025, I.EULER2D_AVG, high_scale=0.02)
+    s.write_state(u0, 0.0)
+    dt = s.step()
+    dto = p.cfl / O.max_rate(p, u0)
+    assert abs(dt - dto) <= 1e-5 * dto
+    ug, _ = s.read_state()
+    s.close()
+    g = I.SplitMix64(98)
+    cells = [(0, 0), (nx - 1, ny - 1), (0, ny - 1), (27, 5), (28, 6), (55, 56), (1023, 1024),
+             (nx - 2, 3), (2047, 777)]
+    cells += [(int(g.uniform(0, nx)), int(g.uniform(0, ny))) for _ in range(24)]
+    for (ci, cj) in cells:
+        ref = _window_step(p, u0, dt, ci, cj)
+        got = ug[:, :, cj * nx + ci]
+        np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
