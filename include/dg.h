@@ -88,13 +88,17 @@ typedef struct {
  *             double-float with compensated error-free updates)
  *   workspace optional caller-owned device buffer of at least dg_workspace_size bytes, aligned to
  *             256 bytes; NULL = the library allocates
- *   tile_rows rows per warp in the 2D stage kernel, 0 = default
- *   tile_warps warps per thread block of the 2D stage kernel, 0 = default (both are tile-shape knobs
- *             for the autotuner; results do not depend on them)
+ *   tile_rows rows per warp in the 2D stage kernel, 0 = default (the height that minimises the
+ *             waves of resident warps times the rows a warp sweeps)
+ *   tile_warps warps per thread block of the 2D stage kernel, 0 = default (the block size with the
+ *             most resident warps per SM); both are tile-shape knobs for the autotuner, results do
+ *             not depend on them
  *   positivity Euler only: 1 = the positivity-preserving limiter of Zhang and Shu after the filter in
  *             every stage (the paper applies it this way in Section 3.2), 0 = off (default): density
- *             and pressure are kept >= min(1e-10, rho_bar, p_bar) at the volume and edge Gauss points
- *             by scaling the modes l >= 1; cell averages are untouched
+ *             and pressure are kept >= min(1e-10, rho_bar, p_bar) (FP64; the FP32 form keeps them
+ *             >= 1e-3 rho_bar and 1e-3 (rho_bar + |E_bar|)) at the volume and edge Gauss points and,
+ *             at degree 3, the Gauss-Lobatto mid-lines, by scaling the modes l >= 1; cell averages
+ *             are untouched; the CFL rate then includes the wave speeds at those points
  *   hybrid    1 = the hybrid limiter of Algorithm 1 (Section 2.4) after every stage instead of the
  *             plain filter: cells whose jump indicator eta_j = ||[rho]||_{dK_j} / (2h) exceeds 1 are
  *             blended with their jump-filtered version by omega_j = (max eta - eta_j)/(max eta - 1),
