@@ -66,6 +66,10 @@ struct Stage1D {
   static constexpr int NQ = K + 1;
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
+  // FP32 form, Euler (three variables): the double-float cell averages of variables 0 and 1 in one
+  // register pair (packed FP32 instructions, bitwise the same results). Degrees 1 and 2 only
+  // (4 M cells: k = 1 0.108 -> 0.105 ms per launch, k = 2 -1 %; k = 3 +0.4 %).
+  static constexpr bool PACK_DF = PR::MIXED && NV == 3 && K <= 2;
   using TB = Tab2D<K, BASIS_Q>;        // the 1D mode l is the x-degree p of the tables
 
   static __device__ __forceinline__ T sd(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
@@ -176,7 +180,7 @@ struct Stage1D {
           ut[v][l] = val;
         }
         ulo[v] = T(0);
-        if constexpr (PR::MIXED) {
+        if constexpr (PR::MIXED && !PACK_DF) {
           // cell average in double-float: u0 + c0 (un0 - u0) + c1 dt/h (F_L - F_R)
           // (a cascaded double-float sum; the face terms are formed bitwise alike on both sides)
           df_acc m0{u[v][0], lo0[v]};
@@ -190,6 +194,39 @@ struct Stage1D {
           const df r0 = m0.result();
           ut[v][0] = r0.hi;
           ulo[v] = r0.lo;
+        }
+      }
+      if constexpr (PACK_DF) {
+        // the same double-float cell averages with variables 0 and 1 in one register pair (each
+        // lane performs the scalar operations), variable 2 scalar
+        {
+          const f2 uh{u[0][0], u[1][0]}, ul{lo0[0], lo0[1]};
+          df2_acc m0{uh, ul};
+          if (a.stage > 0) {
+            df2_acc d{f2{un_[0][0], un_[1][0]}, f2{unlo[0], unlo[1]}};
+            d.add(df2{-uh, -ul});
+            m0.add(df2_mul(dc0, d.result()));
+          }
+          m0.add_prod(dcf, f2{FL[0], FL[1]});
+          m0.add_prod(dcf, -f2{FR[0], FR[1]});
+          const df2 r0 = m0.result();
+          ut[0][0] = r0.hi.x;
+          ut[1][0] = r0.hi.y;
+          ulo[0] = r0.lo.x;
+          ulo[1] = r0.lo.y;
+        }
+        {
+          df_acc m0{u[2][0], lo0[2]};
+          if (a.stage > 0) {
+            df_acc d{un_[2][0], unlo[2]};
+            d.add(df{-u[2][0], -lo0[2]});
+            m0.add(df_mul(dc0, d.result()));
+          }
+          m0.add_prod(dcf, FL[2]);
+          m0.add_prod(dcf, -FR[2]);
+          const df r0 = m0.result();
+          ut[2][0] = r0.hi;
+          ulo[2] = r0.lo;
         }
       }
       T ub[NV];
