@@ -3,6 +3,8 @@
 - Hand-computed single-cell damping factors (1D Burgers P1/P2, 1D Euler P1) from
   Eqs. (para:damp2)-(para:damp21) and the Euler choice c_f^l = beta/(4 l(l+1)) / Hbar (Section 3.1).
 - A 2D Euler Q1 cell whose damping was derived symbolically by tests/golden/make_filter_2d_q1.py
+- A 2D Euler Q2 cell (non-square cells, non-constant neighbours, every mode up to (2,2)) whose
+  damping was derived symbolically by tests/golden/make_filter_2d_q2.py
   (sympy, from Eqs. (para:damp22d)-(para:damp22d1) and Section 3.2), independent of the oracle.
 - Invariants fixed by the method: sigma^0 = 0 (cell averages untouched, Eq. timespli:1dscalar);
   the filter is the identity on a global polynomial of degree <= k; systems take the max over
@@ -104,6 +106,53 @@ def test_euler_2d_q1_symbolic_example():
     for pp, qq, val in _golden_2d():
         m = pp + 2 * qq
         assert s[m, centre] == pytest.approx(val, rel=1e-13)
+
+
+def _q2_example():
+    """The five cells of tests/golden/make_filter_2d_q2.py (read from that script) on its 3x3 mesh."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_q2", os.path.join(GOLDEN, "make_filter_2d_q2.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    p = O.Problem(dim=2, nx=3, ny=3, x0=0, x1=0.3, y0=0, y1=3.0 / 16.0, k=2, eq=O.EQ_EULER,
+                  bc=(O.BC_OUTFLOW,) * 4)
+    u = np.zeros(p.shape)
+    u[0, 0, :] = 1.0            # the four corner cells: a constant physical state (not used)
+    u[3, 0, :] = 2.5
+    for name, cell in mod.INDEX.items():
+        for v in range(4):
+            u[v, :, cell] = 0.0
+            for (pp, qq), c in mod.CELLS[name][v].items():
+                u[v, pp + 3 * qq, cell] = float(c)
+    rows = []
+    with open(os.path.join(GOLDEN, "filter_2d_q2.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            pp, qq, vmax, val = line.split()
+            rows.append((int(pp), int(qq), int(vmax), float(val)))
+    return p, u, rows
+
+
+def test_euler_2d_q2_symbolic_example():
+    # all eight non-constant modes, including (2,1), (1,2), (2,2) (multi-indices up to |a| = 4),
+    # non-square cells, non-constant neighbours, the max over components switching variable
+    p, u, rows = _q2_example()
+    assert len(rows) == 8 and {r[2] for r in rows} == {0, 3}
+    s = O.filter_sigma(p, u)
+    for pp, qq, _, val in rows:
+        assert s[pp + 3 * qq, 4] == pytest.approx(val, rel=1e-13), (pp, qq)
+
+
+def test_euler_2d_q2_symbolic_example_filter_factors():
+    # the filter applies exp(-sigma^{p,q} dt) to each mode and leaves the averages
+    p, u, rows = _q2_example()
+    dt_ = 1e-3
+    out = O.filter(p, u, dt_)
+    np.testing.assert_array_equal(out[:, 0, 4], u[:, 0, 4])
+    for pp, qq, _, val in rows:
+        m = pp + 3 * qq
+        np.testing.assert_allclose(out[:, m, 4], u[:, m, 4] * np.exp(-val * dt_), rtol=1e-13, atol=0)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
