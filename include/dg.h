@@ -69,8 +69,12 @@ typedef enum {
 
 /* Uniform Cartesian mesh (Section 2.1: K_j = [x_{j-1/2}, x_{j+1/2}]; Section 2.2: K_ij).
  * dim 1 uses nx, x0, x1, bc[0..1]; dim 2 also ny, y0, y1, bc[2..3]. bc: x-low, x-high, y-low,
- * y-high. Periodic sides must come in pairs. Outflow: the ghost trace equals the interior trace, so
- * the boundary flux is f(u_interior) and every boundary-face jump is zero. */
+ * y-high. Periodic sides must come in pairs (both sides of an axis alike). Outflow (the paper uses it
+ * without defining it; the reading taken here): the ghost cell beyond a boundary face holds the
+ * constant state equal to the adjacent interior cell's average. The LLF flux at that face is formed
+ * from the interior trace and this constant ghost state (the average of the stage input), and the
+ * filter's jumps there compare the interior cell's u~ and its derivatives with the ghost's constant
+ * u~ average (all derivative jumps are then the interior derivatives themselves). */
 typedef struct {
   int dim, nx, ny;
   double x0, x1, y0, y1;
@@ -156,9 +160,11 @@ DG_API dg_status dg_write_state(dg_solver* s, const double* host_coeffs, size_t 
 DG_API dg_status dg_write_state_device(dg_solver* s, const double* dev_coeffs, size_t n, double t);
 
 /* Copy the canonical FP64 state out (host or device pointer) with its time. Synchronises the
- * solver's stream. n must equal dg_state_size. */
-DG_API dg_status dg_read_state(dg_solver* s, double* host_coeffs, size_t n, double* t);
-DG_API dg_status dg_read_state_device(dg_solver* s, double* dev_coeffs, size_t n, double* t);
+ * solver's stream; the solve itself is not changed (the library refreshes its host copy of the
+ * device step-control scalars and, in the FP32 form, uses its own conversion buffer). n must equal
+ * dg_state_size. */
+DG_API dg_status dg_read_state(const dg_solver* s, double* host_coeffs, size_t n, double* t);
+DG_API dg_status dg_read_state_device(const dg_solver* s, double* dev_coeffs, size_t n, double* t);
 
 /* One SSP-RK3 step with the filter after each stage; dt from the CFL condition (no clipping).
  * Synchronises; *dt_taken (may be NULL) receives the step size. */
@@ -211,11 +217,19 @@ DG_API dg_status dg_kernel_launches(const dg_solver* s, long long* launches);
  *   u_in, u_out: device pointers to canonical FP64 states (dg_state_size doubles); must not overlap.
  *   dt_taken: host pointer or NULL. If non-NULL the call synchronises the stream, stores the step size
  *     and returns DG_ERR_NONPHYSICAL if a cell average became non-physical; if NULL nothing is read
- *     back and the call returns as soon as the kernels are enqueued.
+ *     back and the call returns as soon as the kernels are enqueued. Pass NULL while the stream is
+ *     being captured (a capture cannot synchronise). With NULL a non-physical step is not reported:
+ *     u_out then holds the step's last stage output, and the next call's reset of the shared
+ *     scalars erases the error record.
  *   cuda_stream: the stream the kernels run on (NULL = the legacy default stream).
- * The first call on a device (with that device current) looks up the array's device address once;
- * make that first call before any stream capture. All calls share the array, which keeps the last
- * call's contents (each call resets the scalars it uses): calls that overlap on the GPU race. */
+ *   Arguments are checked as by dg_create (same status codes); also DG_ERR_UNSUPPORTED for the FP32
+ *   form or the hybrid limiter; params->workspace, tile_rows and tile_warps are ignored.
+ * The first call on a device (with that device current) sets the device up once: it checks for an
+ * sm_103 GPU, copies the Gauss rules of the CFL-rate kernel to constant memory and looks up the
+ * array's device address; make that first call before any stream capture. The cached address
+ * belongs to the device's context of that moment: after cudaDeviceReset in the same process it is
+ * stale and no further call may be made on that device. All calls share the array, which keeps the
+ * last call's contents (each call resets the scalars it uses): calls that overlap on the GPU race. */
 DG_API dg_status dg_step_noalloc(const dg_mesh* mesh, int degree, int equation,
                                  const dg_filter_params* params, const double* u_in, double* u_out,
                                  double* dt_taken, void* cuda_stream);

@@ -71,7 +71,7 @@ static int nmodes_of(int dim, int k, int basis) {
   return basis == DG_BASIS_P ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 1);
 }
 
-static dg_status validate(const dg_mesh* m, int k, int eq, const dg_filter_params* p) {
+dg_status dgk::validate_config(const dg_mesh* m, int k, int eq, const dg_filter_params* p) {
   if (!m || !p) return DG_ERR_ARG;
   if (m->dim != 1 && m->dim != 2) return DG_ERR_ARG;
   if (m->nx < 1 || (m->dim == 2 && m->ny < 1)) return DG_ERR_ARG;
@@ -92,9 +92,30 @@ static dg_status validate(const dg_mesh* m, int k, int eq, const dg_filter_param
   return DG_OK;
 }
 
+dg_status dgk::check_device(char* why, size_t why_len) {
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) {
+    snprintf(why, why_len, "cudaGetDevice: %s", cudaGetErrorString(ce));
+    return DG_ERR_CUDA;
+  }
+  int major = 0, minor = 0;
+  ce = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (ce != cudaSuccess) {
+    snprintf(why, why_len, "cudaDeviceGetAttribute: %s", cudaGetErrorString(ce));
+    return DG_ERR_CUDA;
+  }
+  if (major * 10 + minor != 103) {
+    snprintf(why, why_len, "device %d is sm_%d%d; this library is built for sm_103a", dev, major, minor);
+    return DG_ERR_CUDA;
+  }
+  return DG_OK;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static void fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filter_params* p) {
+void dgk::fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filter_params* p) {
   memset(&g, 0, sizeof(g));
   g.dim = m->dim;
   g.nx = m->nx;
@@ -164,7 +185,7 @@ static Layout layout_of(const AuxGeom& g) {
 
 extern "C" dg_status dg_workspace_size(const dg_mesh* mesh, int degree, int equation,
                                        const dg_filter_params* params, size_t* bytes) {
-  dg_status st = validate(mesh, degree, equation, params);
+  dg_status st = validate_config(mesh, degree, equation, params);
   if (st != DG_OK) return st;
   if (!bytes) return DG_ERR_ARG;
   AuxGeom g;
@@ -264,19 +285,12 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
                                const dg_filter_params* params, void* cuda_stream, dg_solver** out) {
   if (!out) return DG_ERR_ARG;
   *out = nullptr;
-  dg_status st = validate(mesh, degree, equation, params);
+  dg_status st = validate_config(mesh, degree, equation, params);
   if (st != DG_OK) return st;
   if (flux != DG_FLUX_LLF) return DG_ERR_UNSUPPORTED;
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
-  cudaDeviceProp prop;
-  CK(cudaGetDeviceProperties(&prop, dev));
-  if (prop.major * 10 + prop.minor != 103) {
-    snprintf(g_last_err, sizeof(g_last_err), "device %s is sm_%d%d; this library is built for sm_103a",
-             prop.name, prop.major, prop.minor);
-    return DG_ERR_CUDA;
-  }
+  st = check_device(g_last_err, sizeof(g_last_err));
+  if (st != DG_OK) return st;
+  cudaError_t ce;
   CK(aux_init_tables());
 
   dg_solver* s = new (std::nothrow) dg_solver();
@@ -478,7 +492,8 @@ dg_status solver_pull_control(dg_solver* s) { return pull_control(s); }
 
 static const void* current_state(const dg_solver* s) { return s->buf[s->h_step & 1]; }
 
-extern "C" dg_status dg_read_state_device(dg_solver* s, double* dst, size_t n, double* t) {
+extern "C" dg_status dg_read_state_device(const dg_solver* cs, double* dst, size_t n, double* t) {
+  dg_solver* s = const_cast<dg_solver*>(cs);   // the solve is unchanged (as dg_read_state)
   if (!s || !dst || n != s->ndof) return DG_ERR_ARG;
   dg_status st = pull_control(s);
   if (st != DG_OK) return st;
@@ -493,7 +508,10 @@ extern "C" dg_status dg_read_state_device(dg_solver* s, double* dst, size_t n, d
   return DG_OK;
 }
 
-extern "C" dg_status dg_read_state(dg_solver* s, double* host, size_t n, double* t) {
+// Reading leaves the solve unchanged; it refreshes the host mirror of the device scalars and uses
+// the conversion buffer, which is why the handle is cast to non-const here.
+extern "C" dg_status dg_read_state(const dg_solver* cs, double* host, size_t n, double* t) {
+  dg_solver* s = const_cast<dg_solver*>(cs);
   if (!s || !host || n != s->ndof) return DG_ERR_ARG;
   dg_status st = pull_control(s);
   if (st != DG_OK) return st;

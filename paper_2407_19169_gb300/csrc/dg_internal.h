@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/dg.h"
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -42,6 +43,13 @@ struct AuxGeom {
 };
 
 cudaError_t aux_init_tables();  // copy Gauss rules to constant memory of the current device
+
+// Argument checks of dg_create (mesh, degree, equation, parameters); DG_OK or the status to return.
+dg_status validate_config(const dg_mesh* m, int k, int eq, const dg_filter_params* p);
+// Geometry and physics of a validated configuration, as the auxiliary kernels see it.
+void fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filter_params* p);
+// DG_OK if the current device is an sm_103 GPU; otherwise DG_ERR_CUDA with the reason in *why.
+dg_status check_device(char* why, size_t why_len);
 cudaError_t launch_project(const AuxGeom& g, int ic, const double* prm, int nprm, int nq,
                            double* canon_out, cudaStream_t s);
 cudaError_t launch_rate(const AuxGeom& g, const void* state, DevScalars* sc, int slot, cudaStream_t s);

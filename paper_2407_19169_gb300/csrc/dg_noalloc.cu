@@ -9,11 +9,15 @@
 //
 // The array: NOALLOC_SCRATCH_BYTES (32 MiB + 256 B) of static device memory, reserved on every GPU
 // that loads this library until the process exits. Host code cannot use the array's name as a
-// device address, so the first call on each device (with that device current) looks the address
-// up with cudaGetSymbolAddress and caches it; make that first call outside any stream capture. All
-// calls share the array and it keeps the last call's contents: each call clears the scalars it
-// needs, and two calls whose kernels overlap on the GPU (different streams, no ordering) race on
-// the array and give undefined results.
+// device address, so the first call on each device (with that device current) sets the device up
+// once: it checks that the device is an sm_103 GPU, copies the Gauss rules that the initial
+// CFL-rate kernel reads into the device's constant memory, and looks the array's address up with
+// cudaGetSymbolAddress, caching it; make that first call outside any stream capture. The cached
+// address belongs to the device's context of that moment: after a cudaDeviceReset in the same
+// process it is stale, so no further call may be made on that device. All calls share the array
+// and it keeps the last call's contents: each call clears the scalars it needs, and two calls whose
+// kernels overlap on the GPU (different streams, no ordering) race on the array and give undefined
+// results.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -57,28 +61,25 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_filter_params* p,
                                      const double* u_in, double* u_out, double* dt_taken,
                                      void* cuda_stream) {
-  if (!m || !p || !u_in || !u_out || u_in == u_out) return DG_ERR_ARG;
-  if (m->dim != 1 && m->dim != 2) return DG_ERR_ARG;
-  if (m->nx < 1 || (m->dim == 2 && m->ny < 1)) return DG_ERR_ARG;
-  if (!(m->x1 > m->x0) || (m->dim == 2 && !(m->y1 > m->y0))) return DG_ERR_ARG;
-  for (int i = 0; i < 2 * m->dim; ++i)
-    if (m->bc[i] != DG_BC_PERIODIC && m->bc[i] != DG_BC_OUTFLOW) return DG_ERR_ARG;
-  if (m->bc[0] != m->bc[1] || (m->dim == 2 && m->bc[2] != m->bc[3])) return DG_ERR_ARG;
-  if (eq < DG_EQ_ADVECTION || eq > DG_EQ_EULER) return DG_ERR_ARG;
-  if (k < 1 || k > 3 || (p->nq != 0 && p->nq != k + 1)) return DG_ERR_UNSUPPORTED;
+  const dg_status vs = validate_config(m, k, eq, p);   // the checks dg_create makes
+  if (vs != DG_OK) return vs;
+  if (!u_in || !u_out || u_in == u_out) return DG_ERR_ARG;
   if (p->precision != DG_PREC_FP64 || p->hybrid) return DG_ERR_UNSUPPORTED;
-  if (!(p->cfl > 0.0) || !(p->gamma > 1.0)) return DG_ERR_ARG;
+  AuxGeom g;
+  fill_geom(g, m, k, eq, p);
   const int dim = m->dim;
-  const int basis = dim == 2 ? p->basis : DG_BASIS_Q;
-  const int nv = eq == DG_EQ_EULER ? (dim == 1 ? 3 : 4) : 1;
-  const int nm = dim == 1 ? k + 1 : (basis == DG_BASIS_P ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 1));
-  const long long ncell = (long long)m->nx * (dim == 2 ? m->ny : 1);
-  const size_t sbytes = align256(sizeof(double) * (size_t)nv * nm * ncell);
+  const int basis = g.basis;
+  const long long ncell = g.ncell;
+  const size_t sbytes = align256(state_bytes(g));
   if (2 * sbytes > NOALLOC_STATE_BYTES) return DG_ERR_BUDGET;   // mesh too large for the array
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return DG_ERR_CUDA;
   if (!g_scratch_addr[dev]) {
+    // once per device: an sm_103 GPU, the Gauss rules in constant memory, the array's address
+    char why[128];
+    if (check_device(why, sizeof(why)) != DG_OK) return DG_ERR_CUDA;
+    if (aux_init_tables() != cudaSuccess) return DG_ERR_CUDA;
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return DG_ERR_CUDA;
     g_scratch_addr[dev] = ptr;
@@ -88,27 +89,6 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
   void* b1 = base;
   void* b2 = base + sbytes;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-
-  AuxGeom g;
-  memset(&g, 0, sizeof(g));
-  g.dim = dim;
-  g.nx = m->nx;
-  g.ny = dim == 2 ? m->ny : 1;
-  g.k = k;
-  g.eq = eq;
-  g.basis = basis;
-  g.prec = PREC_F64;
-  g.pp = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
-  g.nv = nv;
-  g.nm = nm;
-  g.ncell = ncell;
-  g.x0 = m->x0;
-  g.y0 = dim == 2 ? m->y0 : 0.0;
-  g.hx = (m->x1 - m->x0) / m->nx;
-  g.hy = dim == 2 ? (m->y1 - m->y0) / m->ny : 1.0;
-  g.gamma = p->gamma;
-  g.ax = p->adv_speed[0];
-  g.ay = p->adv_speed[1];
 
   noalloc_reset<<<1, 32, 0, st>>>(sc);
   if (cudaGetLastError() != cudaSuccess) return DG_ERR_CUDA;
