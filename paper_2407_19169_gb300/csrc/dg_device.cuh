@@ -463,6 +463,9 @@ __device__ __forceinline__ double vmad(double x, double c, double acc) { return 
 __device__ __forceinline__ f2 vmad(f2 x, float c, f2 acc) {
   return f2of(__ffma2_rn(f2v(x), make_float2(c, c), f2v(acc)));
 }
+__device__ __forceinline__ float vabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double vabs(double x) { return fabs(x); }
+__device__ __forceinline__ f2 vabs(f2 x) { return f2{fabsf(x.x), fabsf(x.y)}; }
 __device__ __forceinline__ float vscale(float x, float c) { return x * c; }
 __device__ __forceinline__ double vscale(double x, double c) { return x * c; }
 __device__ __forceinline__ f2 vscale(f2 x, float c) { return f2of(__fmul2_rn(f2v(x), make_float2(c, c))); }

@@ -23,6 +23,8 @@
 // Face fluxes and jumps at tile seams are recomputed by both tiles with the same operands in the
 // same order, so both sides see bitwise-equal values and conservation holds to roundoff.
 #pragma once
+#include <type_traits>
+
 #include "stage_common.cuh"
 
 namespace dgk {
@@ -204,6 +206,24 @@ struct Stage2D {
   static __device__ __forceinline__ int slot_of(int r) { return ((r % 3) + 3) % 3; }
   static __device__ __forceinline__ T* slot_ptr(T* ws, int s, int v, int m, int lane) {
     return ws + (((s * NV + v) * NME + m) << 5) + lane;
+  }
+  // variable groups of the filter's linear parts: pairs in packed FP32 (VG = f2), else single
+  static constexpr int GW = PACK ? 2 : 1;
+  static constexpr int NG = NV / GW;
+  using VG = typename std::conditional<PACK, f2, T>::type;
+  static __device__ __forceinline__ VG vzero() {
+    if constexpr (PACK) return f2{0.f, 0.f};
+    else return T(0);
+  }
+  template <int G>
+  static __device__ __forceinline__ VG gslot(T* ws, int s, int m, int lane) {
+    if constexpr (PACK) return f2{*slot_ptr(ws, s, 2 * G, m, lane), *slot_ptr(ws, s, 2 * G + 1, m, lane)};
+    else return *slot_ptr(ws, s, G, m, lane);
+  }
+  template <int J>
+  static __device__ __forceinline__ T comp(const VG& x) {
+    if constexpr (PACK) return J == 0 ? x.x : x.y;
+    else return x;
   }
   static __device__ __forceinline__ T shfl_down_t(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ T shfl_up_t(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
@@ -533,68 +553,164 @@ struct Stage2D {
     });
   }
 
-  // eta-derivatives at the horizontal edges of one variable of a cell (or of two variables, VT = f2),
-  // for every x-mode p and order a2: H[p][a2] = sum_q w[p,q] P_q^{(a2)}(-1) (Hm) and (+1) (Hp), split
-  // by the parity of q since P_q^{(a2)}(-1) = (-1)^{q+a2} P_q^{(a2)}(+1). BOTH = false: Hp only.
-  template <bool BOTH, class VT>
-  static __device__ __forceinline__ void eta_ends(const VT (&w)[NM], VT (&Hm)[K + 1][K + 1],
-                                                  VT (&Hp)[K + 1][K + 1]) {
+  // ---- the filter's jumps, edge by edge ----
+  // Across an edge the jump of d^(a1,a2) u at the edge's two corners is a derivative of a jump
+  // polynomial along the edge. For a vertical edge (between this cell and its right neighbour) and
+  // normal order a1: W[q] = sum_p (w_R[p,q] P_p^{(a1)}(-1) - w[p,q] P_p^{(a1)}(+1)), a polynomial
+  // in eta with Legendre coefficients W[q]; its a2-th eta-derivative at eta = -1, +1 is the jump of
+  // d^(a1,a2) at the two corners (the reference scaling (2/h_x)^a1 (2/h_y)^a2 is the positive
+  // factor f applied with the absolute values). P_l^{(r)}(-1) = (-1)^{l+r} P_l^{(r)}(+1), so each
+  // end sum is formed once from its even- and odd-degree parts. Horizontal edges are the same with
+  // the roles of (p, xi) and (q, eta) exchanged.
+
+  // Compile-time structure: the end sum over p of order a1 at fixed q has terms of parity par.
+  static constexpr bool xe(int a1, int q, int par) {
+    for (int pp = a1; pp <= K; ++pp)
+      if ((pp & 1) == par && TB::has(pp, q) && TB::DE[pp * (K + 1) + a1] != 0.0) return true;
+    return false;
+  }
+  static constexpr bool ye(int a2, int pp, int par) { return TB::hq(pp, a2, par); }
+  // the jump polynomial coefficient of order a1 (x-normal) / a2 (y-normal) exists
+  static constexpr bool xw(int a1, int q) { return xe(a1, q, 0) || xe(a1, q, 1); }
+  static constexpr bool yw(int a2, int pp) { return ye(a2, pp, 0) || ye(a2, pp, 1); }
+  // its tangential derivative of order r at +-1 has terms of parity par (over the coefficient index)
+  static constexpr bool xt(int a1, int r, int par) {
+    for (int q = r; q <= K; ++q)
+      if ((q & 1) == par && xw(a1, q) && TB::DE[q * (K + 1) + r] != 0.0) return true;
+    return false;
+  }
+  static constexpr bool yt(int a2, int r, int par) {
+    for (int pp = r; pp <= K; ++pp)
+      if ((pp & 1) == par && yw(a2, pp) && TB::DE[pp * (K + 1) + r] != 0.0) return true;
+    return false;
+  }
+
+  // The end sums of one cell (or a pair of variables, VT = f2) along x: at xi = +1 (xp) and -1 (xm)
+  // for order a1 and coefficient q of the eta-expansion.
+  template <int A1, int Q, class VT>
+  static __device__ __forceinline__ void x_end(const VT (&w)[NM], VT& xp, VT& xm) {
     using S = typename vtraits<VT>::S;
+    constexpr bool he = xe(A1, Q, 0), ho = xe(A1, Q, 1);
+    VT ev = vtraits<VT>::zero(), od = vtraits<VT>::zero();
     sfor<K + 1>([&](auto P) {
-      constexpr int p = decltype(P)::value;
+      constexpr int pp = decltype(P)::value;
+      constexpr int m = TB::MIX[pp * (K + 1) + Q];
+      constexpr double c = TB::DE[pp * (K + 1) + A1];
+      if constexpr (pp >= A1 && m >= 0 && c != 0.0) {
+        if constexpr ((pp & 1) != 0) od = vmad(w[m], (S)c, od);
+        else ev = vmad(w[m], (S)c, ev);
+      }
+    });
+    if constexpr (he && ho) {
+      xp = ev + od;
+      xm = (A1 & 1) ? od - ev : ev - od;
+    } else if constexpr (he) {
+      xp = ev;
+      xm = (A1 & 1) ? -ev : ev;
+    } else {
+      xp = od;
+      xm = (A1 & 1) ? od : -od;
+    }
+  }
+  // along y: at eta = +1 (yp) and -1 (ym) for order a2 and coefficient p of the xi-expansion
+  template <int A2, int PD, class VT>
+  static __device__ __forceinline__ void y_end(const VT (&w)[NM], VT& yp, VT& ym) {
+    using S = typename vtraits<VT>::S;
+    constexpr bool he = ye(A2, PD, 0), ho = ye(A2, PD, 1);
+    VT ev = vtraits<VT>::zero(), od = vtraits<VT>::zero();
+    sfor<K + 1>([&](auto Q) {
+      constexpr int q = decltype(Q)::value;
+      constexpr int m = TB::MIX[PD * (K + 1) + q];
+      constexpr double c = TB::DE[q * (K + 1) + A2];
+      if constexpr (q >= A2 && m >= 0 && c != 0.0) {
+        if constexpr ((q & 1) != 0) od = vmad(w[m], (S)c, od);
+        else ev = vmad(w[m], (S)c, ev);
+      }
+    });
+    if constexpr (he && ho) {
+      yp = ev + od;
+      ym = (A2 & 1) ? od - ev : ev - od;
+    } else if constexpr (he) {
+      yp = ev;
+      ym = (A2 & 1) ? -ev : ev;
+    } else {
+      yp = od;
+      ym = (A2 & 1) ? od : -od;
+    }
+  }
+
+  // |value at +1| + |value at -1| of the R-th derivative of the jump polynomial with coefficients
+  // c[0..K] of normal order NO across an x-edge (DIR = 0) or a y-edge (DIR = 1), times f, into acc.
+  template <int DIR, int NO, int R, class VT>
+  static __device__ __forceinline__ void corner_pair(const VT (&c)[K + 1], typename vtraits<VT>::S f, VT& acc) {
+    using S = typename vtraits<VT>::S;
+    constexpr bool HE = DIR == 0 ? xt(NO, R, 0) : yt(NO, R, 0);
+    constexpr bool HO = DIR == 0 ? xt(NO, R, 1) : yt(NO, R, 1);
+    VT ev = vtraits<VT>::zero(), od = vtraits<VT>::zero();
+    sfor<K + 1>([&](auto Q) {
+      constexpr int q = decltype(Q)::value;
+      constexpr double d = TB::DE[q * (K + 1) + R];
+      constexpr bool present = DIR == 0 ? xw(NO, q) : yw(NO, q);
+      if constexpr (q >= R && d != 0.0 && present) {
+        if constexpr ((q & 1) != 0) od = vmad(c[q], (S)d, od);
+        else ev = vmad(c[q], (S)d, ev);
+      }
+    });
+    if constexpr (HE && HO) {
+      acc = vmad(vabs(ev + od) + vabs(ev - od), f, acc);
+    } else if constexpr (HE) {
+      acc = vmad(vabs(ev), f + f, acc);      // the same magnitude at both corners
+    } else if constexpr (HO) {
+      acc = vmad(vabs(od), f + f, acc);
+    }
+  }
+
+  // Right vertical edge of the cell w: per total order m, sum over |alpha| = m of
+  // f_alpha (|jump at the bottom corner| + |jump at the top corner|) into sv[m].
+  template <class VT>
+  static __device__ __forceinline__ void vertical_jumps(const VT (&w)[NM], VT (&sv)[LMAX + 1], const T (&px)[K + 1],
+                                                        const T (&py)[K + 1]) {
+    sfor<K + 1>([&](auto A1_) {
+      constexpr int a1 = decltype(A1_)::value;
+      VT W[K + 1];
+      sfor<K + 1>([&](auto Q) {
+        constexpr int q = decltype(Q)::value;
+        if constexpr (xw(a1, q)) {
+          VT xp, xm;
+          x_end<a1, q>(w, xp, xm);
+          W[q] = shfl_down_v(xm, 1) - xp;           // the right neighbour's end minus this cell's
+        }
+      });
       sfor<K + 1>([&](auto A2_) {
         constexpr int a2 = decltype(A2_)::value;
-        constexpr bool he = TB::hq(p, a2, 0), ho = TB::hq(p, a2, 1);
-        if constexpr (he || ho) {
-          VT ev = vtraits<VT>::zero(), od = vtraits<VT>::zero();
-          sfor<K + 1>([&](auto Q) {
-            constexpr int q = decltype(Q)::value;
-            constexpr int m = TB::MIX[p * (K + 1) + q];
-            constexpr double c = TB::DE[q * (K + 1) + a2];
-            if constexpr (m >= 0 && c != 0.0) {
-              if constexpr ((q & 1) != 0) od = vmad(w[m], (S)c, od);
-              else ev = vmad(w[m], (S)c, ev);
-            }
-          });
-          if constexpr (he && ho) {
-            Hp[p][a2] = ev + od;
-            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? od - ev : ev - od;
-          } else if constexpr (he) {
-            Hp[p][a2] = ev;
-            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? -ev : ev;
-          } else {
-            Hp[p][a2] = od;
-            if constexpr (BOTH) Hm[p][a2] = (a2 & 1) ? od : -od;
-          }
-        }
+        if constexpr (TB::alpha_ok(a1, a2) && (xt(a1, a2, 0) || xt(a1, a2, 1)))
+          corner_pair<0, a1, a2>(W, px[a1] * py[a2], sv[a1 + a2]);
       });
     });
   }
 
-  // d^(a1,a2) at xi = +1 (plus) and xi = -1 (minus) from one eta-edge row of H
-  template <int A1, int A2, class VT>
-  static __device__ __forceinline__ void xi_ends(const VT (&H)[K + 1][K + 1], VT& plus, VT& minus) {
-    using S = typename vtraits<VT>::S;
-    constexpr bool he = TB::hp(A1, A2, 0), ho = TB::hp(A1, A2, 1);
-    VT ev = vtraits<VT>::zero(), od = vtraits<VT>::zero();
-    sfor<K + 1>([&](auto P) {
-      constexpr int p = decltype(P)::value;
-      constexpr double c = TB::DE[p * (K + 1) + A1];
-      if constexpr (TB::hh(p, A2) && c != 0.0) {
-        if constexpr ((p & 1) != 0) od = vmad(H[p][A2], (S)c, od);
-        else ev = vmad(H[p][A2], (S)c, ev);
-      }
+  // The horizontal edge between the cell below (wb, its top) and the cell above (wa, its bottom).
+  template <class VT>
+  static __device__ __forceinline__ void horizontal_jumps(const VT (&wa)[NM], const VT (&wb)[NM], VT (&sh)[LMAX + 1],
+                                                          const T (&px)[K + 1], const T (&py)[K + 1]) {
+    sfor<K + 1>([&](auto A2_) {
+      constexpr int a2 = decltype(A2_)::value;
+      VT V[K + 1];
+      sfor<K + 1>([&](auto P) {
+        constexpr int pp = decltype(P)::value;
+        if constexpr (yw(a2, pp)) {
+          VT ap, am, bp, bm;
+          y_end<a2, pp>(wa, ap, am);
+          y_end<a2, pp>(wb, bp, bm);
+          V[pp] = am - bp;                          // above at eta = -1 minus below at eta = +1
+        }
+      });
+      sfor<K + 1>([&](auto A1_) {
+        constexpr int a1 = decltype(A1_)::value;
+        if constexpr (TB::alpha_ok(a1, a2) && (yt(a2, a1, 0) || yt(a2, a1, 1)))
+          corner_pair<1, a2, a1>(V, px[a1] * py[a2], sh[a1 + a2]);
+      });
     });
-    if constexpr (he && ho) {
-      plus = ev + od;
-      minus = (A1 & 1) ? od - ev : ev - od;
-    } else if constexpr (he) {
-      plus = ev;
-      minus = (A1 & 1) ? -ev : ev;
-    } else {
-      plus = od;
-      minus = (A1 & 1) ? od : -od;
-    }
   }
 
   // One tile item: strip `strip` (28 output columns) and row chunk `chunk` of one instance, with step
@@ -951,166 +1067,66 @@ struct Stage2D {
         if (a.filter_on && (need_v || filt_row)) {
           T eta_v = T(0), eta_h = T(0);
           const int s1 = slot_of(t - 1), s2 = slot_of(t - 2);
-          if constexpr (PACK) {
-            // two variables per register pair; each lane forms the scalar chain of the loop below
+          // groups of variables (pairs in packed FP32, else one variable): the jumps are linear in
+          // the modes, each group's chain is the scalar chain of every variable in it
+          sfor<NG>([&](auto G_) {
+            constexpr int g = decltype(G_)::value;
+            const VG z = vzero();
+            VG w1[NM], w2[NM];
 #pragma unroll
-            for (int vp = 0; vp < NV / 2; ++vp) {
-              const int v0 = 2 * vp, v1 = 2 * vp + 1;
-              const f2 z2{0.f, 0.f};
-              f2 uv[NM], u2[NM];
+            for (int m = 0; m < NM; ++m) {
+              w1[m] = gslot<g>(ws, s1, m, lane);
+              w2[m] = gslot<g>(ws, s2, m, lane);
+            }
+            // ghost rows and columns: the constant state of the adjacent interior cell's u~ average
+            if (g1) {
+              w1[0] = w2[0];
 #pragma unroll
-              for (int m = 0; m < NM; ++m) {
-                uv[m] = f2{*slot_ptr(ws, s1, v0, m, lane), *slot_ptr(ws, s1, v1, m, lane)};
-                u2[m] = f2{*slot_ptr(ws, s2, v0, m, lane), *slot_ptr(ws, s2, v1, m, lane)};
-              }
-              if (g1) {
-                uv[0] = u2[0];
+              for (int m = 1; m < NM; ++m) w1[m] = z;
+            }
+            if (g2) {
+              w2[0] = w1[0];
 #pragma unroll
-                for (int m = 1; m < NM; ++m) uv[m] = z2;
-              }
-              if (g2) {
-                u2[0] = uv[0];
+              for (int m = 1; m < NM; ++m) w2[m] = z;
+            }
+            if (edge_strip) {                                   // warp-uniform: a strip at an outflow side
+              const VG v_r = shfl_down_v(w1[0], 1), v_l = shfl_up_v(w1[0], 1);
+              const VG w_r = shfl_down_v(w2[0], 1), w_l = shfl_up_v(w2[0], 1);
+              if (gcol) {
+                w1[0] = x < 0 ? v_r : v_l;
+                w2[0] = x < 0 ? w_r : w_l;
 #pragma unroll
-                for (int m = 1; m < NM; ++m) u2[m] = z2;
-              }
-              if (edge_strip) {
-                const f2 v_r = shfl_down_v(uv[0], 1), v_l = shfl_up_v(uv[0], 1);
-                const f2 w_r = shfl_down_v(u2[0], 1), w_l = shfl_up_v(u2[0], 1);
-                if (gcol) {
-                  uv[0] = x < 0 ? v_r : v_l;
-                  u2[0] = x < 0 ? w_r : w_l;
-#pragma unroll
-                  for (int m = 1; m < NM; ++m) uv[m] = u2[m] = z2;
-                }
-              }
-              f2 Hb[K + 1][K + 1], Ht[K + 1][K + 1], H2[K + 1][K + 1];
-              eta_ends<true>(uv, Hb, Ht);
-              eta_ends<false>(u2, H2, H2);
-              f2 svr[LMAX + 1], sh[LMAX + 1];
-#pragma unroll
-              for (int l = 0; l <= LMAX; ++l) svr[l] = sh[l] = z2;
-              sfor<K + 1>([&](auto B2) {
-                constexpr int a2 = decltype(B2)::value;
-                sfor<K + 1>([&](auto B1) {
-                  constexpr int a1 = decltype(B1)::value;
-                  if constexpr (TB::alpha_ok(a1, a2)) {
-                    f2 c00, c01, c10, c11, t01, t11;
-                    xi_ends<a1, a2>(Hb, c10, c00);
-                    xi_ends<a1, a2>(Ht, c11, c01);
-                    xi_ends<a1, a2>(H2, t11, t01);
-                    const T f = px[a1] * py[a2];
-                    constexpr int l = a1 + a2;
-                    if (need_v) {
-                      const f2 d0 = c10 - shfl_down_v(c00, 1), d1 = c11 - shfl_down_v(c01, 1);
-                      svr[l] = vmad(f2{fabsf(d0.x) + fabsf(d1.x), fabsf(d0.y) + fabsf(d1.y)}, f, svr[l]);
-                    }
-                    const f2 e0 = c00 - t01, e1 = c10 - t11;
-                    sh[l] = vmad(f2{fabsf(e0.x) + fabsf(e1.x), fabsf(e0.y) + fabsf(e1.y)}, f, sh[l]);
-                  }
-                });
-              });
-              f2 av = z2, shc = z2;
-#pragma unroll
-              for (int l = 0; l <= LMAX; ++l) {
-                shc = vmad(sh[l], wy[l], shc);
-                if (need_v) av = vmad(shfl_up_v(svr[l], 1) + svr[l], wx[l], av);
-                if (l == 0) {
-                  if (a.hybrid && vp == 0) {
-                    eta_v = av.x * T(0.5) * inv_hx;
-                    eta_h = shc.x * T(0.5) * inv_hy;
-                  }
-                  continue;
-                }
-                T* q0 = wq + ((v0 * LMAX + (l - 1)) << 5) + lane;
-                T* q1 = wq + ((v1 * LMAX + (l - 1)) << 5) + lane;
-                if (filt_row) {
-                  sig[l] = nan_max(sig[l], *q0 + by2 * shc.x);
-                  sig[l] = nan_max(sig[l], *q1 + by2 * shc.y);
-                }
-                if (need_v) {
-                  *q0 = bx1 * av.x + by1 * shc.x;
-                  *q1 = bx1 * av.y + by1 * shc.y;
-                }
+                for (int m = 1; m < NM; ++m) w1[m] = w2[m] = z;
               }
             }
-          } else {
-#pragma unroll(PR::MIXED ? NV : 1)
-            for (int v = 0; v < NV; ++v) {                        // FP32 form: the variables' chains interleave
-              T uv[NM], u2[NM];
+            // per total order m: sum over |alpha| = m of the scaled corner jumps, the right vertical
+            // edge of row t-1 (sv) and the face (t-2 | t-1) (sh)
+            VG sv[LMAX + 1], sh[LMAX + 1];
 #pragma unroll
-              for (int m = 0; m < NM; ++m) {
-                uv[m] = *slot_ptr(ws, s1, v, m, lane);
-                u2[m] = *slot_ptr(ws, s2, v, m, lane);
-              }
-              // ghost rows and columns: the constant state of the adjacent interior cell's u~ average
-              if (g1) {
-                uv[0] = u2[0];
+            for (int l = 0; l <= LMAX; ++l) sv[l] = sh[l] = z;
+            if (need_v) vertical_jumps(w1, sv, px, py);
+            horizontal_jumps(w1, w2, sh, px, py);
+            VG av = z, shc = z;
 #pragma unroll
-                for (int m = 1; m < NM; ++m) uv[m] = T(0);
-              }
-              if (g2) {
-                u2[0] = uv[0];
-#pragma unroll
-                for (int m = 1; m < NM; ++m) u2[m] = T(0);
-              }
-              if (edge_strip) {                                   // warp-uniform: a strip at an outflow side
-                const T v_r = shfl_down_t(uv[0], 1), v_l = shfl_up_t(uv[0], 1);
-                const T w_r = shfl_down_t(u2[0], 1), w_l = shfl_up_t(u2[0], 1);
-                if (gcol) {
-                  uv[0] = x < 0 ? v_r : v_l;
-                  u2[0] = x < 0 ? w_r : w_l;
-#pragma unroll
-                  for (int m = 1; m < NM; ++m) uv[m] = u2[m] = T(0);
+            for (int l = 0; l <= LMAX; ++l) {
+              shc = vmad(sh[l], wy[l], shc);
+              if (need_v) av = vmad(shfl_up_v(sv[l], 1) + sv[l], wx[l], av);
+              if (l == 0) {
+                // density: edge-averaged value jumps, J^V / (2 h_x) and the face (t-2 | t-1) / (2 h_y)
+                if (a.hybrid && g == 0) {
+                  eta_v = comp<0>(av) * T(0.5) * inv_hx;
+                  eta_h = comp<0>(shc) * T(0.5) * inv_hy;
                 }
+                continue;
               }
-              // eta-derivatives at the horizontal edges: row t-1 at eta = -1 and +1, row t-2 at +1
-              T Hb[K + 1][K + 1], Ht[K + 1][K + 1], H2[K + 1][K + 1];
-              eta_ends<true>(uv, Hb, Ht);
-              eta_ends<false>(u2, H2, H2);
-              T svr[LMAX + 1], sh[LMAX + 1];
-#pragma unroll
-              for (int l = 0; l <= LMAX; ++l) svr[l] = sh[l] = T(0);
-              sfor<K + 1>([&](auto B2) {
-                constexpr int a2 = decltype(B2)::value;
-                sfor<K + 1>([&](auto B1) {
-                  constexpr int a1 = decltype(B1)::value;
-                  if constexpr (TB::alpha_ok(a1, a2)) {
-                    // corner values of d^alpha u~: c00 = (xi,eta) = (-1,-1), c01 = (-1,+1), c10, c11;
-                    // t01, t11: the top corners of row t-2
-                    T c00, c01, c10, c11, t01, t11;
-                    xi_ends<a1, a2>(Hb, c10, c00);
-                    xi_ends<a1, a2>(Ht, c11, c01);
-                    xi_ends<a1, a2>(H2, t11, t01);
-                    // physical derivatives: the same positive factor (2/hx)^a1 (2/hy)^a2 on both sides
-                    const T f = px[a1] * py[a2];
-                    constexpr int l = a1 + a2;
-                    if (need_v) {
-                      const T n0 = shfl_down_t(c00, 1), n1 = shfl_down_t(c01, 1);
-                      svr[l] += f * (fabs(c10 - n0) + fabs(c11 - n1));
-                    }
-                    sh[l] += f * (fabs(c00 - t01) + fabs(c10 - t11));
-                  }
-                });
-              });
-              T av = T(0), shc = T(0);
-#pragma unroll
-              for (int l = 0; l <= LMAX; ++l) {
-                shc += wy[l] * sh[l];
-                if (need_v) av += wx[l] * (shfl_up_t(svr[l], 1) + svr[l]);
-                if (l == 0) {
-                  // density: edge-averaged value jumps, J^V / (2 h_x) and the face (t-2 | t-1) / (2 h_y)
-                  if (a.hybrid && v == 0) {
-                    eta_v = av * T(0.5) * inv_hx;
-                    eta_h = shc * T(0.5) * inv_hy;
-                  }
-                  continue;
-                }
+              sfor<GW>([&](auto J_) {
+                constexpr int j = decltype(J_)::value, v = g * GW + j;
                 T* q = wq + ((v * LMAX + (l - 1)) << 5) + lane;
-                if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * shc);   // Q of row t-2 + its top face
-                if (need_v) *q = bx1 * av + by1 * shc;                      // Q of row t-1 (bottom face)
-              }
+                if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * comp<j>(shc));   // Q of row t-2 + its top face
+                if (need_v) *q = bx1 * comp<j>(av) + by1 * comp<j>(shc);          // Q of row t-1 (bottom face)
+              });
             }
-          }
+          });
           if (a.hybrid) {
             if (filt_row) eta2 = weta[lane] + eta_h;             // row t-2: + its top face
             if (need_v) weta[lane] = eta_v + eta_h;               // row t-1: vertical faces + bottom face

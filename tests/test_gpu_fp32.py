@@ -4,6 +4,7 @@ Bars: relative L1 <= 1e-5 on smooth runs; on shock runs the L1 error against the
 within 2% of the FP64 path's error; mass conserved to double-float roundoff.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ import oracle as O
 from paper_2407_19169_gb300 import _native as N
 from paper_2407_19169_gb300 import inputs as I
 
-from _helpers import pair, rel_l1
+from _helpers import l1_vs_finer, pair, rel_l1
 
 pytestmark = pytest.mark.gpu
 INF = float("inf")
@@ -55,7 +56,7 @@ def test_burgers_1d_smooth():
     assert rel_l1(p, ug, uo) <= 1e-5
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_riemann_1d_shock_error_within_2_percent(k):
     seed = 1
     prm = I.riemann1d_params(seed)
@@ -68,6 +69,39 @@ def test_riemann_1d_shock_error_within_2_percent(k):
         assert t == 0.1
         errs[prec] = O.errors(p, ug, O.EX_RIEMANN1D, prm, 0.1, var=0)[0]
     assert abs(errs[N.PREC_FP32_MIXED] - errs[N.PREC_FP64]) <= 0.02 * errs[N.PREC_FP64]
+
+
+def _first_quadrant_seed():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "quadrant_seeds.txt")) as f:
+        for line in f:
+            if not line.startswith("#") and line.strip():
+                sd, ok, _ = line.split()
+                if int(ok):
+                    return int(sd)
+    raise RuntimeError("no accepted quadrant seed")
+
+
+def test_quadrant_2d_q2_shock_error_within_2_percent():
+    # The benchmark's problem type (2D Euler Q2, seeded four-quadrant Riemann data, outflow) on a
+    # 48^2 mesh to T = 0.03: the FP32 form's L1 error against a 2x finer FP64 oracle run (96^2) is
+    # within 2% of the FP64 path's error against the same reference, for every variable.
+    T = 0.03
+    prm = I.quadrant_params(_first_quadrant_seed())
+    pf = O.Problem(dim=2, nx=96, ny=96, k=2, eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4)
+    uf, tf, _ = O.advance(pf, O.project(pf, O.IC_QUADRANT2D, prm), 0.0, T)
+    assert tf == T
+    errs = {}
+    for prec in (N.PREC_FP64, N.PREC_FP32_MIXED):
+        pc, s = pair(dim=2, nx=48, ny=48, k=2, eq="euler", bc="outflow", precision=prec)
+        s.set_initial(N.IC_QUADRANT2D, prm)
+        s.advance_to(T)
+        ug, t = s.read_state()
+        assert t == T
+        errs[prec] = [l1_vs_finer(pc, ug, pf, uf, var=v) for v in range(4)]
+    for v in range(4):
+        e64, e32 = errs[N.PREC_FP64][v], errs[N.PREC_FP32_MIXED][v]
+        print("quadrant Q2 48^2 var %d: L1 vs 96^2 oracle FP64 %.6e FP32 %.6e ratio %.5f" % (v, e64, e32, e32 / e64))
+        assert abs(e32 - e64) <= 0.02 * e64
 
 
 def test_mass_conserved_fp32_form_2d():
