@@ -57,6 +57,16 @@ typedef enum { DG_FLUX_LLF = 0 } dg_flux;
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 } dg_bc;
 typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
 typedef enum { DG_BASIS_Q = 0, DG_BASIS_P = 1 } dg_basis;
+/* Damping coefficients of the filter (Section 2.1):
+ *   DG_FILTER_JUMP    the paper's mode-dependent jump filter: the coefficient of a mode of total degree
+ *                     l takes the jumps of the derivatives up to order l (Eqs. para:damp2-para:damp21,
+ *                     2D: para:damp22d-para:damp22d1)
+ *   DG_FILTER_GLOBAL  one coefficient for all modes, from the jumps of every derivative order the space
+ *                     holds (Eq. para:damp; 2D: eq:2dalljumpvis1, orders up to 2k for Q^k), with the same
+ *                     c_f factors as the jump filter
+ *   DG_FILTER_OEDG    the OEDG damping as Section 2.1 restates it: weights (2m+1)/m! h^m, 1/h scaling,
+ *                     c_f = beta / (2 (2k-1) ||u - avg(u)||_inf) per variable (not yet available) */
+typedef enum { DG_FILTER_JUMP = 0, DG_FILTER_GLOBAL = 1, DG_FILTER_OEDG = 2 } dg_filter_kind;
 
 /* Initial conditions projected on the device (L2 projection, Gauss rule with nq_init points). */
 typedef enum {
@@ -108,7 +118,8 @@ typedef struct {
  *             blended with their jump-filtered version by omega_j = (max eta - eta_j)/(max eta - 1),
  *             the others keep the unfiltered DG solution. Needs enabled = 1 and positivity = 0
  *             (DG_ERR_UNSUPPORTED otherwise); not available in dg_batch_run or dg_step_noalloc.
- *             0 = off (default) */
+ *             0 = off (default)
+ *   filter_kind DG_FILTER_JUMP (default), DG_FILTER_GLOBAL or DG_FILTER_OEDG (dg_filter_kind) */
 typedef struct {
   int enabled;
   double cfl;
@@ -123,6 +134,7 @@ typedef struct {
   int tile_warps;
   int positivity;
   int hybrid;
+  int filter_kind;
 } dg_filter_params;
 
 typedef struct dg_solver dg_solver; /* opaque, library-owned */

@@ -29,6 +29,7 @@ BC_PERIODIC, BC_OUTFLOW = 0, 1
 BASIS_Q, BASIS_P = 0, 1
 IC_SINE, IC_RIEMANN1D, IC_ENTROPY1D, IC_QUADRANT2D, IC_VORTEX2D, IC_ZERO = range(6)
 EX_BURGERS, EX_ADVECTION, EX_RIEMANN1D, EX_ENTROPY1D, EX_VORTEX2D = range(5)
+FILTER_JUMP, FILTER_GLOBAL, FILTER_OEDG = range(3)
 
 
 class _Problem(C.Structure):
@@ -37,7 +38,7 @@ class _Problem(C.Structure):
                 ("bc", C.c_int * 4), ("k", C.c_int), ("basis", C.c_int), ("eq", C.c_int),
                 ("gamma", C.c_double), ("adv", C.c_double * 2), ("filter", C.c_int),
                 ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int), ("positivity", C.c_int),
-                ("hybrid", C.c_int)]
+                ("hybrid", C.c_int), ("filter_kind", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -61,6 +62,7 @@ class Problem:
     filter_dt_mode: int = 0
     positivity: int = 0
     hybrid: int = 0
+    filter_kind: int = 0
 
     def c(self) -> _Problem:
         s = _Problem()
@@ -122,6 +124,7 @@ def lib():
             "orc_dt": (D, [P, dp, D, D]), "orc_residual": (None, [P, dp, dp]),
             "orc_filter": (None, [P, dp, D, dp]), "orc_filter_sigma": (None, [P, dp, dp]),
             "orc_positivity": (None, [P, dp]),
+            "orc_oedg_norms": (None, [P, dp, dp]),
             "orc_jump_indicator": (None, [P, dp, dp]), "orc_hybrid": (None, [P, dp, D, dp]),
             "orc_rk_stage": (None, [P, I, dp, dp, D, dp]), "orc_step": (I, [P, dp, D]),
             "orc_advance": (I, [P, dp, D, D, C.c_long, dp, C.POINTER(C.c_long)]),
@@ -233,6 +236,15 @@ def filter(p: Problem, u, dt_: float) -> np.ndarray:  # noqa: A001 - the paper's
     out = np.zeros_like(u)
     pc = p.c()
     lib().orc_filter(C.byref(pc), _dp(u), float(dt_), _dp(out))
+    return out
+
+
+def oedg_norms(p: Problem, u) -> np.ndarray:
+    """||u_v - avg(u_v)||_inf per variable (the OEDG coefficient's normaliser)."""
+    u = _arr(u)
+    out = np.zeros(p.nvars)
+    pc = p.c()
+    lib().orc_oedg_norms(C.byref(pc), _dp(u), _dp(out))
     return out
 
 

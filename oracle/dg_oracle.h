@@ -36,6 +36,14 @@ extern "C" {
 enum { ORC_EQ_ADVECTION = 0, ORC_EQ_BURGERS = 1, ORC_EQ_EULER = 2 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
 enum { ORC_BASIS_Q = 0, ORC_BASIS_P = 1 };
+/* Damping of the filter (Section 2.1):
+ *   ORC_FILTER_JUMP   the mode-dependent jump filter, Eqs. (para:damp2)-(para:damp21) (the paper's scheme)
+ *   ORC_FILTER_GLOBAL one damping coefficient for all modes, Eq. (para:damp): sigma_j from the jumps of
+ *                     every derivative order, sigma_j^l = sigma_j (2/h)^2 l(l+1), c_f = c_f^l
+ *   ORC_FILTER_OEDG   the OEDG damping as the paper writes it in its notation:
+ *                     sigma^{l,OE} = c_f^OE (h ||[u]|| + sum_{m=1..l} (2m+1)/m! h^{m+1} ||[d^m u]||) / h^2,
+ *                     c_f^OE = beta / (2 (2k-1) ||u - avg(u)||_{L^inf(Omega)}) (0 if u = avg(u)) */
+enum { ORC_FILTER_JUMP = 0, ORC_FILTER_GLOBAL = 1, ORC_FILTER_OEDG = 2 };
 
 /* Initial-condition kinds for the L2 projection (Section 3 examples and synthetic workloads). */
 enum {
@@ -64,6 +72,7 @@ typedef struct {
                               1: the stage's own effective step (dt, dt/4, 2dt/3) */
   int positivity;          /* Euler: 1 = Zhang-Shu positivity-preserving limiter after the filter */
   int hybrid;              /* 1 = hybrid limiter of Algorithm 1 (jump filter as the low-order part) */
+  int filter_kind;         /* ORC_FILTER_*: the damping coefficients of the filter */
 } orc_problem;
 
 /* ---- basis (orc_basis.c) ---- */
@@ -92,6 +101,7 @@ void   orc_positivity(const orc_problem* p, double* u);            /* Zhang-Shu 
 void   orc_jump_indicator(const orc_problem* p, const double* u, double* eta); /* Algorithm 1 eta_j */
 void   orc_hybrid(const orc_problem* p, const double* u, double dt, double* out);  /* Algorithm 1 */
 void   orc_filter_sigma(const orc_problem* p, const double* u, double* sigma); /* sigma^l per cell, l=0..lmax */
+void   orc_oedg_norms(const orc_problem* p, const double* u, double* ninf);   /* ||u_v - avg u_v||_inf */
 void   orc_rk_stage(const orc_problem* p, int s, const double* un, const double* us, double dt, double* out);
 int    orc_step(const orc_problem* p, double* u, double dt);  /* one SSP-RK3 step in place; 0 = ok */
 int    orc_advance(const orc_problem* p, double* u, double t0, double T, long max_steps,

@@ -57,6 +57,12 @@ long orc_state_size(const orc_problem* p) {
   return (long)orc_nvars(p) * orc_nmodes(p) * (long)p->nx * (p->dim == 2 ? p->ny : 1);
 }
 
+static double fact(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
 static void make_ctx(const orc_problem* p, ctx_t* c) {
   memset(c, 0, sizeof(*c));
   c->k = p->k;
@@ -265,7 +271,8 @@ static double end_deriv_1d(const ctx_t* c, const double* u, int v, long cell, in
 }
 
 /* sigma^l of Eqs. (para:damp2)-(para:damp21), maximised over components (Eq. para:dampsystems1d). */
-static void sigma_1d(const orc_problem* p, const ctx_t* c, const double* u, long i, double* sig) {
+static void sigma_1d(const orc_problem* p, const ctx_t* c, const double* u, long i, const double* ninf,
+                     double* sig) {
   const double h = c->hx;
   double J[ORC_MAXNV][ORC_MAXK + 1];
   long il = neighbour(p, (int)i, 0, 0, 0), ir = neighbour(p, (int)i, 0, 0, 1);
@@ -286,11 +293,27 @@ static void sigma_1d(const orc_problem* p, const ctx_t* c, const double* u, long
   double Hbar = orc_enthalpy(p, ubar);               /* Euler: 1/H_bar factor (Section 3.1) */
   sig[0] = 0.0;                                      /* sigma^0 = 0: cell averages untouched */
   for (int l = 1; l <= c->k; ++l) {
+    if (p->filter_kind == ORC_FILTER_OEDG) {
+      /* sigma^{l,OE} = sigma^{OE}_{j,l} / h^2, each component with its own c_f^OE */
+      double best = 0.0;
+      for (int v = 0; v < c->nv; ++v) {
+        double cf = ninf[v] > 0.0 ? beta / (2.0 * (2 * c->k - 1) * ninf[v]) : 0.0;
+        double s = h * J[v][0];
+        for (int m = 1; m <= l; ++m) s += (2.0 * m + 1.0) / fact(m) * pow(h, m + 1) * J[v][m];
+        s = cf * s / (h * h);
+        if (s > best || isnan(s)) best = s;
+      }
+      sig[l] = best;
+      continue;
+    }
+    /* the jump filter sums the jumps up to order l (Eq. para:damp21); the global coefficient of
+     * Eq. (para:damp) takes every order up to k, for every mode */
+    const int top = p->filter_kind == ORC_FILTER_GLOBAL ? c->k : l;
     double cf = beta / (4.0 * l * (l + 1)) / Hbar;   /* c_f^l */
     double best = 0.0;
     for (int v = 0; v < c->nv; ++v) {
       double s = h * J[v][0];
-      for (int m = 1; m <= l; ++m) s += m * (m + 1) * pow(h, m + 1) * J[v][m];
+      for (int m = 1; m <= top; ++m) s += m * (m + 1) * pow(h, m + 1) * J[v][m];
       s *= cf;                                       /* sigma_{j,l}(u^(v)) */
       if (s > best || isnan(s)) best = s;
     }
@@ -308,7 +331,8 @@ static double corner_deriv_2d(const ctx_t* c, const double* u, int v, long cell,
 
 /* sigma for every mode of a 2D cell, Eqs. (para:damp22d)-(para:damp22d1) with the Euler choice of
  * (c_fx, c_fy) of Section 3.2 (scalar laws: H_bar = 1), edge norms by the trapezoidal rule. */
-static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long cell, double* sig) {
+static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long cell, const double* ninf,
+                     double* sig) {
   const double hx = c->hx, hy = c->hy;
   const int k = c->k, nx = p->nx;
   int i = (int)(cell % nx), j = (int)(cell / nx);
@@ -344,13 +368,42 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
   for (int m = 0; m < c->nm; ++m) {
     int pp = c->mp[m], qq = c->mq[m], l = pp + qq;
     if (l == 0) { sig[m] = 0.0; continue; }
+    if (p->filter_kind == ORC_FILTER_OEDG) {
+      /* The paper states the OEDG damping in 1D only; in 2D each direction takes its edges as the
+       * jump filter does: sigma = c_f^OE [beta^x (h_x J^V_0 + sum_{m=1..l} (2m+1)/m! h_x^{m+1}
+       * S^V_m) / h_x^2 + beta^y (the same with H, h_y) / h_y^2] with beta / c_f^OE shared, so that
+       * y-invariant data give the 1D value. */
+      double best = 0.0;
+      for (int v = 0; v < c->nv; ++v) {
+        double cf = ninf[v] > 0.0 ? 1.0 / (2.0 * (2 * k - 1) * ninf[v]) : 0.0;
+        double sx = hx * JV[v][0][0], sy = hy * JH[v][0][0];
+        for (int mm = 1; mm <= l; ++mm) {
+          double tv = 0.0, th = 0.0;
+          for (int a1 = 0; a1 <= k; ++a1) {
+            int a2 = mm - a1;
+            if (a2 < 0 || a2 > k) continue;
+            tv += JV[v][a1][a2];
+            th += JH[v][a1][a2];
+          }
+          sx += (2.0 * mm + 1.0) / fact(mm) * pow(hx, mm + 1) * tv;
+          sy += (2.0 * mm + 1.0) / fact(mm) * pow(hy, mm + 1) * th;
+        }
+        double s = cf * (bx * sx / (hx * hx) + by * sy / (hy * hy));
+        if (s > best || isnan(s)) best = s;
+      }
+      sig[m] = best;
+      continue;
+    }
+    /* the global coefficient of Eq. (para:damp) (2D: Eq. eq:2dalljumpvis1) takes every derivative
+     * order the space holds (|alpha| up to 2k with alpha_1, alpha_2 <= k), for every mode */
+    const int top = p->filter_kind == ORC_FILTER_GLOBAL ? 2 * k : l;
     double lam = pp * (pp + 1) + qq * (qq + 1);      /* lambda_{p,q} */
     double cfx = hy * bx / (4.0 * lam * Hbar);       /* c_{f,x}^{p,q} */
     double cfy = hx * by / (4.0 * lam * Hbar);       /* c_{f,y}^{p,q} */
     double best = 0.0;
     for (int v = 0; v < c->nv; ++v) {
       double sx = hx * JV[v][0][0], sy = hy * JH[v][0][0];
-      for (int mm = 1; mm <= l; ++mm) {
+      for (int mm = 1; mm <= top; ++mm) {
         double tv = 0.0, th = 0.0;
         for (int a1 = 0; a1 <= k; ++a1) {            /* |alpha| = mm */
           int a2 = mm - a1;
@@ -368,13 +421,43 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
   }
 }
 
+/* ||u_v - avg(u_v)||_{L^inf(Omega)} per variable for the OEDG coefficient: avg is the domain average
+ * (the mean of the cell averages on the uniform mesh), the maximum is taken at the volume Gauss
+ * points of every cell (the k+1-point rule per direction). */
+static void oedg_norms(const orc_problem* p, const ctx_t* c, const double* u, double* ninf) {
+  for (int v = 0; v < c->nv; ++v) {
+    double avg = 0.0;
+    for (long cell = 0; cell < c->ncell; ++cell) avg += U(u, v, 0, cell);
+    avg /= (double)c->ncell;
+    double mx = 0.0;
+    for (long cell = 0; cell < c->ncell; ++cell)
+      for (int a = 0; a < c->nq; ++a)
+        for (int b = 0; b < (p->dim == 2 ? c->nq : 1); ++b) {
+          double val = 0.0;
+          for (int m = 0; m < c->nm; ++m)
+            val += U(u, v, m, cell) * c->P[c->mp[m]][a] * (p->dim == 2 ? c->P[c->mq[m]][b] : 1.0);
+          double d = fabs(val - avg);
+          if (d > mx || isnan(d)) mx = d;
+        }
+    ninf[v] = mx;
+  }
+}
+
+void orc_oedg_norms(const orc_problem* p, const double* u, double* ninf) {
+  ctx_t c;
+  make_ctx(p, &c);
+  oedg_norms(p, &c, u, ninf);
+}
+
 void orc_filter_sigma(const orc_problem* p, const double* u, double* sigma) {
   ctx_t c;
   make_ctx(p, &c);
+  double ninf[ORC_MAXNV] = {0};
+  if (p->filter_kind == ORC_FILTER_OEDG) oedg_norms(p, &c, u, ninf);
 #pragma omp parallel for num_threads(g_threads) schedule(static)
   for (long cell = 0; cell < c.ncell; ++cell) {
     double s[ORC_MAXNM];
-    if (p->dim == 1) sigma_1d(p, &c, u, cell, s); else sigma_2d(p, &c, u, cell, s);
+    if (p->dim == 1) sigma_1d(p, &c, u, cell, ninf, s); else sigma_2d(p, &c, u, cell, ninf, s);
     for (int m = 0; m < c.nm; ++m) sigma[(long)m * c.ncell + cell] = s[m];
   }
 }
@@ -384,10 +467,12 @@ void orc_filter(const orc_problem* p, const double* u, double dt, double* out) {
   ctx_t cc;
   make_ctx(p, &cc);
   const ctx_t* c = &cc;
+  double ninf[ORC_MAXNV] = {0};
+  if (p->filter_kind == ORC_FILTER_OEDG) oedg_norms(p, c, u, ninf);
 #pragma omp parallel for num_threads(g_threads) schedule(static)
   for (long cell = 0; cell < c->ncell; ++cell) {
     double s[ORC_MAXNM];
-    if (p->dim == 1) sigma_1d(p, c, u, cell, s); else sigma_2d(p, c, u, cell, s);
+    if (p->dim == 1) sigma_1d(p, c, u, cell, ninf, s); else sigma_2d(p, c, u, cell, ninf, s);
     for (int m = 0; m < c->nm; ++m) {
       double f = (m == 0) ? 1.0 : exp(-s[m] * dt);
       for (int v = 0; v < c->nv; ++v) U(out, v, m, cell) = f * U(u, v, m, cell);

@@ -21,6 +21,7 @@ FLUX_LLF = 0
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 PREC_FP64, PREC_FP32_MIXED = 0, 1
 BASIS_Q, BASIS_P = 0, 1
+FILTER_JUMP, FILTER_GLOBAL, FILTER_OEDG = 0, 1, 2
 IC_SINE, IC_RIEMANN1D, IC_ENTROPY1D, IC_QUADRANT2D, IC_VORTEX2D = range(5)
 
 EXPORTED = ["dg_status_string", "dg_last_error", "dg_params_default", "dg_workspace_size", "dg_create",
@@ -40,7 +41,7 @@ class Params(C.Structure):
                 ("adv_speed", C.c_double * 2), ("basis", C.c_int), ("nq", C.c_int), ("precision", C.c_int),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("tile_rows", C.c_int),
                 ("tile_warps", C.c_int), ("positivity", C.c_int),
-                ("hybrid", C.c_int)]
+                ("hybrid", C.c_int), ("filter_kind", C.c_int)]
 
 
 class DGError(RuntimeError):
@@ -122,7 +123,7 @@ class Solver:
     def __init__(self, dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(BC_PERIODIC,) * 4, k=2,
                  eq=EQ_BURGERS, filter=1, cfl=0.1, gamma=1.4, adv=(1.0, 0.0), basis=BASIS_Q,
                  precision=PREC_FP64, stream=None, tile_rows=0, workspace=None, tile_warps=0,
-                 positivity=0, hybrid=0):
+                 positivity=0, hybrid=0, filter_kind=FILTER_JUMP):
         L = load()
         self.mesh = Mesh(dim, nx, ny, x0, x1, y0, y1, (C.c_int * 4)(*bc))
         self.params = Params()
@@ -137,6 +138,7 @@ class Solver:
         self.params.tile_warps = tile_warps
         self.params.positivity = positivity
         self.params.hybrid = hybrid
+        self.params.filter_kind = filter_kind
         self._workspace = workspace  # keep a caller tensor alive
         if workspace is not None:
             self.params.workspace = workspace.data_ptr()

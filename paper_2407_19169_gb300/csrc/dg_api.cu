@@ -89,6 +89,9 @@ dg_status dgk::validate_config(const dg_mesh* m, int k, int eq, const dg_filter_
   if (!(p->cfl > 0.0) || !(p->gamma > 1.0)) return DG_ERR_ARG;
   if ((long long)m->nx * (m->dim == 2 ? m->ny : 1) > (1LL << 31)) return DG_ERR_UNSUPPORTED;
   if (p->hybrid && (!p->enabled || p->positivity)) return DG_ERR_UNSUPPORTED;
+  if (p->filter_kind < DG_FILTER_JUMP || p->filter_kind > DG_FILTER_OEDG) return DG_ERR_ARG;
+  if (p->filter_kind == DG_FILTER_OEDG) return DG_ERR_UNSUPPORTED;
+  if (p->hybrid && p->filter_kind != DG_FILTER_JUMP) return DG_ERR_UNSUPPORTED;
   return DG_OK;
 }
 
@@ -302,7 +305,7 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
   s->dim = mesh->dim;
   s->basis = mesh->dim == 2 ? params->basis : DG_BASIS_Q;
   s->prec = params->precision == DG_PREC_FP64 ? PREC_F64 : PREC_F32M;
-  s->filter_on = params->enabled ? 1 : 0;
+  s->filter_on = params->enabled ? FILT_JUMP + params->filter_kind : FILT_OFF;
   s->positivity = (params->positivity && equation == DG_EQ_EULER) ? 1 : 0;
   s->hybrid = params->hybrid ? 1 : 0;
   s->cfl = params->cfl;

@@ -18,6 +18,10 @@ enum { EQ_ADV = 0, EQ_BURG = 1, EQ_EULER = 2 };
 enum { BASIS_Q = 0, BASIS_P = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
 
+// The stage kernels' filter switch: off, or the damping coefficients of DG_FILTER_JUMP,
+// DG_FILTER_GLOBAL, DG_FILTER_OEDG (include/dg.h) plus one.
+enum { FILT_OFF = 0, FILT_JUMP = 1, FILT_GLOBAL = 2, FILT_OEDG = 3 };
+
 // Error bits of DevScalars::err.
 enum : unsigned { ERRB_NONPHYS = 1u, ERRB_RATE = 2u };
 

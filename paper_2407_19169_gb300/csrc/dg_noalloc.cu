@@ -114,7 +114,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.c0 = C0[s];
       a.c1 = C1[s];
       a.stage = s;
-      a.filter_on = p->enabled ? 1 : 0;
+      a.filter_on = p->enabled ? FILT_JUMP + p->filter_kind : FILT_OFF;
       a.gamma = p->gamma;
       a.ax = p->adv_speed[0];
       a.cfl = p->cfl;
@@ -155,7 +155,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.c0 = C0[s];
       a.c1 = C1[s];
       a.stage = s;
-      a.filter_on = p->enabled ? 1 : 0;
+      a.filter_on = p->enabled ? FILT_JUMP + p->filter_kind : FILT_OFF;
       a.gamma = p->gamma;
       a.ax = p->adv_speed[0];
       a.ay = p->adv_speed[1];

@@ -28,7 +28,7 @@ struct Stage1DArgs {
   int bc;            // BC_PERIODIC or BC_OUTFLOW (both ends alike)
   double c0, c1;
   int stage;
-  int filter_on;
+  int filter_on;      // FILT_OFF, FILT_JUMP or FILT_GLOBAL
   double gamma, ax, cfl;
   int nwarps;
   int positivity;    // Euler: Zhang-Shu limiter after the filter
@@ -286,12 +286,18 @@ struct Stage1D {
             run[v] += wpow[l] * J[v][l];
             best = (run[v] > best || run[v] != run[v]) ? run[v] : best;
           }
-          const T fac = exp(-(bx * inv_h * invH * best) * dt);
-          facs[l] = fac;
-          if (!a.hybrid) {
+          facs[l] = exp(-(bx * inv_h * invH * best) * dt);
+        }
+        if (a.filter_on == FILT_GLOBAL) {
+          // one coefficient for every mode, from the jumps of all derivative orders (Eq. para:damp)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) ut[v][l] *= fac;
-          }
+          for (int l = 1; l < NM - 1; ++l) facs[l] = facs[NM - 1];
+        }
+        if (!a.hybrid) {
+#pragma unroll
+          for (int l = 1; l < NM; ++l)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ut[v][l] *= facs[l];
         }
         if (a.hybrid) {
           // Algorithm 1: eta = (|[rho]_{j-1/2}| + |[rho]_{j+1/2}|) / (2 h); u^DG stored as it is

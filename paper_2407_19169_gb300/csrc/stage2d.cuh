@@ -39,7 +39,7 @@ struct Stage2DArgs {
   int bcx, bcy;      // BC_PERIODIC or BC_OUTFLOW (both sides of an axis alike)
   double c0, c1;     // u~ = c0 u^n + c1 (u^(s) + dt R)
   int stage;         // 0, 1, 2
-  int filter_on;
+  int filter_on;      // FILT_OFF, FILT_JUMP or FILT_GLOBAL
   double gamma, ax, ay, cfl;
   int H;             // rows per chunk
   int nstrips, nchunks;
@@ -133,9 +133,18 @@ struct Stage2D {
   using ST = Store<PR, NV, NM>;
   using TB = Tab2D<K, BASIS>;
 
-  // per-warp shared memory: 3 row slots of u~, the partial damping Q[v][l-1] of one row and the
-  // partial jump indicator of one row (hybrid limiter)
-  static constexpr size_t warp_bytes() { return sizeof(T) * (3 * NV * NME + NV * LMAX + 1) * 32; }
+  // Row slots of u~ (rows t, t-1, t-2). Packed FP32 form: per lane, one contiguous block per (slot,
+  // pair of variables) of NMEP pair words {v0[m], v1[m]} (m = NM: the low words of the two cell
+  // averages), read and written with 128-bit shared-memory instructions; the lane stride LS is
+  // 4 (mod 8) words, so the 8 lanes of each phase of a 128-bit access hit distinct banks. Otherwise
+  // one row of 32 lanes per (slot, v, m).
+  static constexpr int NMEP = (NME + 1) & ~1;
+  static constexpr int PW = 3 * (NV / 2) * NMEP * 2;
+  static constexpr int LS = PW + (12 - PW % 8) % 8;
+  static constexpr int SLOT_WORDS = PACK ? 32 * LS : 3 * NV * NME * 32;
+  // per-warp shared memory: the row slots, the partial damping Q[v][l-1] of one row and the partial
+  // jump indicator of one row (hybrid limiter)
+  static constexpr size_t warp_bytes() { return sizeof(T) * (SLOT_WORDS + (NV * LMAX + 1) * 32); }
   static constexpr size_t slot_bytes_per_warp() { return warp_bytes(); }
 
   // ---- compile-time tables of the positivity limiter's points (evaluated by the front end) ----
@@ -205,7 +214,24 @@ struct Stage2D {
   // row slot of row r (rows >= -2 occur; keep the index in 0..2)
   static __device__ __forceinline__ int slot_of(int r) { return ((r % 3) + 3) % 3; }
   static __device__ __forceinline__ T* slot_ptr(T* ws, int s, int v, int m, int lane) {
-    return ws + (((s * NV + v) * NME + m) << 5) + lane;
+    if constexpr (PACK) return ws + lane * LS + ((s * (NV / 2) + v / 2) * NMEP + m) * 2 + (v & 1);
+    else return ws + (((s * NV + v) * NME + m) << 5) + lane;
+  }
+  // packed form: the block of a pair of variables, and its NMEP pair words in registers
+  static __device__ __forceinline__ float4* pblock(T* ws, int s, int vp, int lane) {
+    return (float4*)(ws + lane * LS + (s * (NV / 2) + vp) * NMEP * 2);
+  }
+  static __device__ __forceinline__ void pload(const float4* b, f2 (&w)[NMEP]) {
+#pragma unroll
+    for (int i = 0; i < NMEP / 2; ++i) {
+      const float4 x = b[i];
+      w[2 * i] = f2{x.x, x.y};
+      w[2 * i + 1] = f2{x.z, x.w};
+    }
+  }
+  static __device__ __forceinline__ void pstore(float4* b, const f2 (&w)[NMEP]) {
+#pragma unroll
+    for (int i = 0; i < NMEP / 2; ++i) b[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x, w[2 * i + 1].y);
   }
   // variable groups of the filter's linear parts: pairs in packed FP32 (VG = f2), else single
   static constexpr int GW = PACK ? 2 : 1;
@@ -724,7 +750,7 @@ struct Stage2D {
 
     const T dt = (T)dtd;
     const int lane = threadIdx.x & 31;
-    T* wq = ws + 3 * NV * NME * 32;                               // Q[v][l-1] of the next row to filter
+    T* wq = ws + SLOT_WORDS;                                      // Q[v][l-1] of the next row to filter
     T* weta = wq + NV * LMAX * 32;                                // hybrid: eta of the next row, partial
     T my_eta = T(0);
     const int nx = a.nx, ny = a.ny;
@@ -831,7 +857,7 @@ struct Stage2D {
               const int s = slot_of(t - 1);
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
-                if constexpr (PR::MIXED && !PACK_DF) {
+                if constexpr (PR::MIXED && !PACK) {
                   df_acc acc0{*slot_ptr(ws, s, v, 0, lane), *slot_ptr(ws, s, v, NM, lane)};
                   acc0.add_prod(dfy, -Mh[v][0]);
                   const df r0 = acc0.result();
@@ -851,30 +877,29 @@ struct Stage2D {
 #pragma unroll
                 for (int vp = 0; vp < NV / 2; ++vp) {
                   const int v0 = 2 * vp, v1 = v0 + 1;
+                  f2 blk[NMEP];
+                  pload(pblock(ws, s, vp, lane), blk);
                   if constexpr (PACK_DF) {
-                    T* h0 = slot_ptr(ws, s, v0, 0, lane);
-                    T* h1 = slot_ptr(ws, s, v1, 0, lane);
-                    T* l0 = slot_ptr(ws, s, v0, NM, lane);
-                    T* l1 = slot_ptr(ws, s, v1, NM, lane);
-                    df2_acc acc0{f2{*h0, *h1}, f2{*l0, *l1}};
+                    df2_acc acc0{blk[0], blk[NM]};
                     acc0.add_prod(dfy, -f2{Mh[v0][0], Mh[v1][0]});
                     const df2 r0 = acc0.result();
-                    *h0 = r0.hi.x;
-                    *h1 = r0.hi.y;
-                    *l0 = r0.lo.x;
-                    *l1 = r0.lo.y;
+                    blk[0] = r0.hi;
+                    blk[NM] = r0.lo;
+                  } else {
+                    // the scalar double-float update of each of the two averages
+                    df_acc a0{blk[0].x, blk[NM].x}, a1{blk[0].y, blk[NM].y};
+                    a0.add_prod(dfy, -Mh[v0][0]);
+                    a1.add_prod(dfy, -Mh[v1][0]);
+                    const df r0 = a0.result(), r1 = a1.result();
+                    blk[0] = f2{r0.hi, r1.hi};
+                    blk[NM] = f2{r0.lo, r1.lo};
                   }
                   f2 ms[K + 1];
 #pragma unroll
                   for (int p = 0; p <= K; ++p) ms[p] = vscale(f2{Mh[v0][p], Mh[v1][p]}, sy);
 #pragma unroll
-                  for (int m = 1; m < NM; ++m) {
-                    T* p0 = slot_ptr(ws, s, v0, m, lane);
-                    T* p1 = slot_ptr(ws, s, v1, m, lane);
-                    const f2 r = vmad(ms[PP[m]], -(T)MINV[m], f2{*p0, *p1});
-                    *p0 = r.x;
-                    *p1 = r.y;
-                  }
+                  for (int m = 1; m < NM; ++m) blk[m] = vmad(ms[PP[m]], -(T)MINV[m], blk[m]);
+                  pstore(pblock(ws, s, vp, lane), blk);
                 }
               }
             }
@@ -979,22 +1004,25 @@ struct Stage2D {
           const int s = slot_of(t);
           T un_[NV][NM], unlo[NV];
           if (a.stage > 0) ST::load(a.un, a.ncell, cell, un_, unlo);
+          // cell average in double-float from the edge integrals, each formed once per edge:
+          // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B [- Phi_T at the next row])
+          auto df_average = [&](auto v) -> df {          // (instantiated by the FP32 form only)
+            df_acc m0{u[v][0], lo0[v]};
+            if (a.stage > 0) {
+              df_acc d{un_[v][0], unlo[v]};
+              d.add(df{-u[v][0], -lo0[v]});
+              const df dd = d.result();
+              m0.add(df_mul(dfc0, dd));
+            }
+            m0.add_prod(dfx, ML[v][0]);
+            m0.add_prod(dfx, -MR[v][0]);
+            m0.add_prod(dfy, Mh[v][0]);
+            return m0.result();
+          };
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            if constexpr (PR::MIXED && !PACK_DF) {
-              // cell average in double-float from the edge integrals, each formed once per edge:
-              // u0 + c0 (un0 - u0) + c1 dt/(2h) (Phi_L - Phi_R + Phi_B [- Phi_T at the next row])
-              df_acc m0{u[v][0], lo0[v]};
-              if (a.stage > 0) {
-                df_acc d{un_[v][0], unlo[v]};
-                d.add(df{-u[v][0], -lo0[v]});
-                const df dd = d.result();
-                m0.add(df_mul(dfc0, dd));
-              }
-              m0.add_prod(dfx, ML[v][0]);
-              m0.add_prod(dfx, -MR[v][0]);
-              m0.add_prod(dfy, Mh[v][0]);
-              const df r0 = m0.result();
+            if constexpr (PR::MIXED && !PACK) {
+              const df r0 = df_average(v);
               *slot_ptr(ws, s, v, 0, lane) = r0.hi;
               *slot_ptr(ws, s, v, NM, lane) = r0.lo;
             }
@@ -1013,6 +1041,7 @@ struct Stage2D {
 #pragma unroll
             for (int vp = 0; vp < NV / 2; ++vp) {
               const int v0 = 2 * vp, v1 = v0 + 1;
+              f2 blk[NMEP];
               if constexpr (PACK_DF) {
                 // the double-float cell averages of the scalar branch, two variables per pair
                 const f2 uh{u[v0][0], u[v1][0]}, ul{lo0[v0], lo0[v1]};
@@ -1026,19 +1055,22 @@ struct Stage2D {
                 m0.add_prod(dfx, -f2{MR[v0][0], MR[v1][0]});
                 m0.add_prod(dfy, f2{Mh[v0][0], Mh[v1][0]});
                 const df2 r0 = m0.result();
-                *slot_ptr(ws, s, v0, 0, lane) = r0.hi.x;
-                *slot_ptr(ws, s, v1, 0, lane) = r0.hi.y;
-                *slot_ptr(ws, s, v0, NM, lane) = r0.lo.x;
-                *slot_ptr(ws, s, v1, NM, lane) = r0.lo.y;
+                blk[0] = r0.hi;
+                blk[NM] = r0.lo;
+              } else {
+                const df r0 = df_average(v0), r1 = df_average(v1);
+                blk[0] = f2{r0.hi, r1.hi};
+                blk[NM] = f2{r0.lo, r1.lo};
               }
 #pragma unroll
               for (int m = 1; m < NM; ++m) {
                 f2 val{u[v0][m], u[v1][m]};
                 if (a.stage > 0) val = vmad(f2{un_[v0][m], un_[v1][m]} - val, c0, val);
-                val = vmad(f2{acc[v0][m], acc[v1][m]}, (T)MINV[m], val);
-                *slot_ptr(ws, s, v0, m, lane) = val.x;
-                *slot_ptr(ws, s, v1, m, lane) = val.y;
+                blk[m] = vmad(f2{acc[v0][m], acc[v1][m]}, (T)MINV[m], val);
               }
+#pragma unroll
+              for (int m = NM + 1; m < NMEP; ++m) blk[m] = f2{0.f, 0.f};
+              pstore(pblock(ws, s, vp, lane), blk);
             }
           }
         }
@@ -1057,7 +1089,17 @@ struct Stage2D {
         if (r1) {
           T ub[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) ub[v] = *slot_ptr(ws, slot_of(t - 1), v, 0, lane);
+          for (int v = 0; v < NV; ++v) {
+            if constexpr (PACK) {
+              if ((v & 1) == 0) {
+                const float4 x = pblock(ws, slot_of(t - 1), v / 2, lane)[0];   // {v, v+1} of mode 0 (and 1)
+                ub[v] = x.x;
+                ub[v + 1] = x.y;
+              }
+            } else {
+              ub[v] = *slot_ptr(ws, slot_of(t - 1), v, 0, lane);
+            }
+          }
           avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx1, by1, invH1, phys1);
         }
         T sig[LMAX + 1];
@@ -1073,10 +1115,21 @@ struct Stage2D {
             constexpr int g = decltype(G_)::value;
             const VG z = vzero();
             VG w1[NM], w2[NM];
+            if constexpr (PACK) {
+              f2 b1[NMEP], b2[NMEP];
+              pload(pblock(ws, s1, g, lane), b1);
+              pload(pblock(ws, s2, g, lane), b2);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) {
-              w1[m] = gslot<g>(ws, s1, m, lane);
-              w2[m] = gslot<g>(ws, s2, m, lane);
+              for (int m = 0; m < NM; ++m) {
+                w1[m] = b1[m];
+                w2[m] = b2[m];
+              }
+            } else {
+#pragma unroll
+              for (int m = 0; m < NM; ++m) {
+                w1[m] = gslot<g>(ws, s1, m, lane);
+                w2[m] = gslot<g>(ws, s2, m, lane);
+              }
             }
             // ghost rows and columns: the constant state of the adjacent interior cell's u~ average
             if (g1) {
@@ -1137,17 +1190,37 @@ struct Stage2D {
           const int ty2 = pery ? ((t - 2) % ny + ny) % ny : t - 2;
           const long long cell2 = (long long)ty2 * nx + xc;
           T uo[NV][NM], lo[NV];
+          if constexpr (PACK) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
+            for (int vp = 0; vp < NV / 2; ++vp) {
+              f2 blk[NMEP];
+              pload(pblock(ws, s2, vp, lane), blk);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) uo[v][m] = *slot_ptr(ws, s2, v, m, lane);
-            if constexpr (PR::MIXED) lo[v] = *slot_ptr(ws, s2, v, NM, lane);
-            else lo[v] = T(0);
+              for (int m = 0; m < NM; ++m) {
+                uo[2 * vp][m] = blk[m].x;
+                uo[2 * vp + 1][m] = blk[m].y;
+              }
+              lo[2 * vp] = blk[NM].x;
+              lo[2 * vp + 1] = blk[NM].y;
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+#pragma unroll
+              for (int m = 0; m < NM; ++m) uo[v][m] = *slot_ptr(ws, s2, v, m, lane);
+              if constexpr (PR::MIXED) lo[v] = *slot_ptr(ws, s2, v, NM, lane);
+              else lo[v] = T(0);
+            }
           }
           if (a.filter_on) {
             T fac[LMAX + 1];
 #pragma unroll
             for (int l = 1; l <= LMAX; ++l) fac[l] = exp(-(sig[l] * invH2) * dt);
+            if (a.filter_on == FILT_GLOBAL) {
+              // one coefficient for every mode, from the jumps of all derivative orders (Eq. para:damp)
+#pragma unroll
+              for (int l = 1; l < LMAX; ++l) fac[l] = fac[LMAX];
+            }
             if (a.hybrid) {
               // u^DG is stored as it is; the blend kernel limits the troubled cells
               hybrid_record<T, LMAX>(a.hyb, a.ncell, cell2, out_lane, eta2, fac);

@@ -35,15 +35,16 @@ def parity_bar(p, u0, uo, steps, case=""):
 
 
 def pair(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, k=2, eq="burgers", bc="periodic",
-         basis="Q", filt=1, cfl=0.1, adv=(1.0, 0.5), precision=N.PREC_FP64, tile_rows=0):
+         basis="Q", filt=1, cfl=0.1, adv=(1.0, 0.5), precision=N.PREC_FP64, tile_rows=0,
+         filter_kind=N.FILTER_JUMP):
     """(oracle Problem, GPU Solver) for the same configuration."""
     b = BC[bc]
     p = O.Problem(dim=dim, nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, bc=(b,) * 4, k=k,
                   basis=O.BASIS_Q if basis == "Q" else O.BASIS_P, eq=EQ[eq][0], filter=filt, cfl=cfl,
-                  adv=adv)
+                  adv=adv, filter_kind=filter_kind)
     s = N.Solver(dim=dim, nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, bc=(b,) * 4, k=k, eq=EQ[eq][1],
                  filter=filt, cfl=cfl, adv=adv, basis=N.BASIS_Q if basis == "Q" else N.BASIS_P,
-                 precision=precision, tile_rows=tile_rows)
+                 precision=precision, tile_rows=tile_rows, filter_kind=filter_kind)
     return p, s
 
 

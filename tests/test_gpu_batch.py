@@ -57,6 +57,42 @@ def test_batch_equals_alone():
         assert rel(ub, ua) <= 1e-12, (sp, rel(ub, ua))
 
 
+def test_batch_against_the_oracle():
+    """A batched mix (1D and 2D, degrees 1-3, one dg_batch_run) against the FP64 oracle: smooth
+    instances within the FP32 form's 1e-5 relative L1; the 1D Riemann instance's L1 density error
+    against the exact solution within 2% of the oracle's own error at the same step count."""
+    import math
+
+    import oracle as O
+    from _helpers import rel_l1
+    steps = 30
+    specs = [dict(kind="entropy1d", n=160, k=2), dict(kind="vortex2d", n=40, k=1),
+             dict(kind="vortex2d", n=28, k=3), dict(kind="riemann1d", n=400, k=3, seed=1),
+             dict(kind="entropy1d", n=90, k=3)]
+    mix = [make(sp) for sp in specs]
+    u0s = [s.read_state()[0] for s in mix]
+    assert N.batch_run(mix, steps) == 0
+    for sp, s, u0 in zip(specs, mix, u0s):
+        ub, tb = s.read_state()
+        if sp["kind"] == "entropy1d":
+            p = O.Problem(dim=1, nx=sp["n"], k=sp["k"], eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4)
+        elif sp["kind"] == "vortex2d":
+            p = O.Problem(dim=2, nx=sp["n"], ny=sp["n"], x0=0, x1=10, y0=-5, y1=5, k=sp["k"],
+                          eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4)
+        else:
+            p = O.Problem(dim=1, nx=sp["n"], k=sp["k"], eq=O.EQ_EULER, bc=(O.BC_OUTFLOW,) * 4)
+        uo, to, no = O.advance(p, u0, 0.0, math.inf, steps)
+        assert no == steps
+        if sp["kind"] == "riemann1d":
+            prm = I.riemann1d_params(sp["seed"])
+            eb = O.errors(p, ub, O.EX_RIEMANN1D, prm, tb, var=0)[0]
+            eo = O.errors(p, uo, O.EX_RIEMANN1D, prm, to, var=0)[0]
+            assert abs(eb - eo) <= 0.02 * eo, (sp, eb, eo)
+        else:
+            assert abs(tb - to) <= 1e-6 * to
+            assert rel_l1(p, ub, uo) <= 1e-5, (sp, rel_l1(p, ub, uo))
+
+
 def test_batch_per_instance_end_times():
     mix = [make(sp) for sp in SPECS[:6]]
     ends = [0.002, 0.004, 0.003, 0.0005, 0.01, 0.02]

@@ -67,6 +67,97 @@ def test_euler_p1_hand_example():
     assert out[0, 1, 1] / u[0, 1, 1] == pytest.approx(0.996625090832968, rel=1e-14)
 
 
+def test_global_sigma_burgers_p2_hand_example():
+    # Eq. (para:damp) with c_f = c_f^l: one coefficient for every mode from the jumps of all orders
+    # up to k, sigma^l = beta / h^2 (h J_0 + 2 h^2 J_1 + 6 h^3 J_2) = 435 for l = 1 and l = 2 (the
+    # mode-dependent filter's sigma^2 of the same cell)
+    p = three_cells(2)
+    p.filter_kind = O.FILTER_GLOBAL
+    u = np.zeros(p.shape)
+    u[0, 0, :] = [0.0, 1.0, 1.0]
+    u[0, 1, :] = [0.0, 0.5, 0.0]
+    u[0, 2, :] = [0.0, 0.25, 0.0]
+    s = O.filter_sigma(p, u)
+    assert s[1, 1] == pytest.approx(435.0, rel=1e-14)
+    assert s[2, 1] == pytest.approx(435.0, rel=1e-14)
+
+
+def test_oedg_burgers_p2_hand_example():
+    # Section 2.1's OEDG form: sigma^{l,OE} = c (h J_0 + sum_{m<=l} (2m+1)/m! h^{m+1} J_m) / h^2,
+    # c = beta / (2 (2k-1) N), N = ||u - avg(u)||_inf. Cell averages (0, 1, 1): avg = 2/3; the largest
+    # deviation is at the centre cell's Gauss point xi = +sqrt(3/5), where u = 1 + 0.5 sqrt(3/5)
+    # + 0.25 P_2 = 1 + 0.5 sqrt(3/5) + 0.1. With J = (1.5, 30, 600), h = 0.1, beta = 1, k = 2:
+    # sigma^1 = (0.15 + 0.9) / 0.01 / (6 N) = 17.5 / N, sigma^2 = (1.05 + 1.5) / 0.01 / (6 N) = 42.5 / N
+    p = three_cells(2)
+    p.filter_kind = O.FILTER_OEDG
+    u = np.zeros(p.shape)
+    u[0, 0, :] = [0.0, 1.0, 1.0]
+    u[0, 1, :] = [0.0, 0.5, 0.0]
+    u[0, 2, :] = [0.0, 0.25, 0.0]
+    N = 1.0 + 0.5 * math.sqrt(0.6) + 0.1 - 2.0 / 3.0
+    assert O.oedg_norms(p, u)[0] == pytest.approx(N, rel=1e-14)
+    s = O.filter_sigma(p, u)
+    assert s[1, 1] == pytest.approx(17.5 / N, rel=1e-13)
+    assert s[2, 1] == pytest.approx(42.5 / N, rel=1e-13)
+    assert s[0, 1] == 0.0
+
+
+def test_oedg_euler_p1_hand_example():
+    # Only the density jumps (J_0 = 0.2, J_1 = 4 as in the jump-filter example); each component
+    # has its own normaliser: N_rho = 0.1 / sqrt(3) (the density's deviation at the Gauss points of
+    # the centre cell, every average being 1), N = 0 for momentum and energy (their c^OE is 0).
+    # sigma^1 = sqrt(1.4) / (2 N_rho) (0.1 * 0.2 + 3 * 0.01 * 4) / 0.01 = 70 sqrt(4.2); no 1/Hbar
+    p = three_cells(1, O.EQ_EULER)
+    p.filter_kind = O.FILTER_OEDG
+    u = np.zeros(p.shape)
+    u[0, 0, :] = 1.0
+    u[2, 0, :] = 2.5
+    u[0, 1, 1] = 0.1
+    n = O.oedg_norms(p, u)
+    assert n[0] == pytest.approx(0.1 / math.sqrt(3.0), rel=1e-14) and n[1] == 0.0 and n[2] == 0.0
+    s = O.filter_sigma(p, u)
+    assert s[1, 1] == pytest.approx(70.0 * math.sqrt(4.2), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [O.FILTER_GLOBAL, O.FILTER_OEDG])
+def test_variants_2d_reduce_to_1d_on_y_invariant_data(kind):
+    # y-invariant data: no horizontal jumps, the vertical edge averages equal the 1D end jumps. The
+    # global coefficient keeps the jump filter's 2D scaling (h_x times the 1D value); the OEDG form
+    # divides each direction by its own h, so it gives the 1D value itself.
+    k = 2
+    rng = np.random.default_rng(5)
+    p1 = O.Problem(dim=1, nx=7, x0=0.0, x1=0.7, k=k, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, filter_kind=kind)
+    p2 = O.Problem(dim=2, nx=7, ny=4, x0=0.0, x1=0.7, y0=0.0, y1=0.4, k=k, eq=O.EQ_EULER,
+                   bc=(O.BC_PERIODIC,) * 4, filter_kind=kind)
+    u1 = np.zeros(p1.shape)
+    u1[0, 0] = rng.uniform(1.0, 2.0, 7)
+    u1[1, 0] = rng.uniform(-0.3, 0.3, 7)
+    u1[2, 0] = rng.uniform(4.0, 6.0, 7)
+    u1[:, 1:] = rng.uniform(-0.05, 0.05, (3, k, 7))
+    u2 = np.zeros(p2.shape)
+    for j in range(4):
+        cells = slice(7 * j, 7 * j + 7)
+        u2[0, :k + 1, cells] = u1[0]          # modes (p, 0): p = 0..k
+        u2[1, :k + 1, cells] = u1[1]
+        u2[3, :k + 1, cells] = u1[2]
+    s1 = O.filter_sigma(p1, u1)
+    s2 = O.filter_sigma(p2, u2)
+    scale = p2.hx if kind == O.FILTER_GLOBAL else 1.0
+    for pdeg in range(1, k + 1):
+        np.testing.assert_allclose(s2[pdeg, :7], scale * s1[pdeg], rtol=1e-12)
+
+
+def test_global_sigma_q2_symbolic_example():
+    # the global coefficient takes every derivative order (|alpha| <= 4 for Q2) for every mode; with
+    # Section 3.2's c_f the lambda_{p,q} cancels, so every mode gets the symbolic example's (2,2) value
+    p, u, rows = _q2_example()
+    p.filter_kind = O.FILTER_GLOBAL
+    top = [val for pp, qq, _, val in rows if (pp, qq) == (2, 2)][0]
+    s = O.filter_sigma(p, u)
+    for pp, qq, _, _ in rows:
+        assert s[pp + 3 * qq, 4] == pytest.approx(top, rel=1e-13)
+
+
 def test_outflow_ghost_is_the_cell_average():
     # outflow boundary reading: the ghost cell holds the constant state of the interior cell's
     # average. Burgers P1, h = 0.1, boundary cell [1, 0.5], neighbours [1, 0]: left face jumps
