@@ -64,8 +64,13 @@ typedef enum { DG_BASIS_Q = 0, DG_BASIS_P = 1 } dg_basis;
  *   DG_FILTER_GLOBAL  one coefficient for all modes, from the jumps of every derivative order the space
  *                     holds (Eq. para:damp; 2D: eq:2dalljumpvis1, orders up to 2k for Q^k), with the same
  *                     c_f factors as the jump filter
- *   DG_FILTER_OEDG    the OEDG damping as Section 2.1 restates it: weights (2m+1)/m! h^m, 1/h scaling,
- *                     c_f = beta / (2 (2k-1) ||u - avg(u)||_inf) per variable (not yet available) */
+ *   DG_FILTER_OEDG    the OEDG damping as Section 2.1 restates it: sigma^l = max_v c_v (h ||[u_v]|| +
+ *                     sum_{m<=l} (2m+1)/m! h^{m+1} ||[d^m u_v]||) / h^2, c_v = beta / (2 (2k-1)
+ *                     ||u_v - avg(u_v)||_inf), the norm over the volume Gauss points of the whole mesh
+ *                     (c_v = 0 for a constant variable); 2D: each direction with its own beta, h and
+ *                     edges. Burgers and Euler, not with the positivity or hybrid limiter, not in
+ *                     dg_batch_run or dg_step_noalloc (DG_ERR_UNSUPPORTED). Each stage then runs one more
+ *                     kernel, because the coefficient needs the stage solution of the whole mesh */
 typedef enum { DG_FILTER_JUMP = 0, DG_FILTER_GLOBAL = 1, DG_FILTER_OEDG = 2 } dg_filter_kind;
 
 /* Initial conditions projected on the device (L2 projection, Gauss rule with nq_init points). */

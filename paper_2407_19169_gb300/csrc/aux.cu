@@ -324,6 +324,72 @@ cudaError_t launch_hybrid_blend(const AuxGeom& g, void* state, const HybridOut& 
   return cudaGetLastError();
 }
 
+// OEDG damping (Section 2.1 as the paper restates it), after the stage kernel stored u~ and the jump
+// sums: per variable v the normaliser N_v = ||u_v - avg u_v||_inf = max(max_v - avg_v, avg_v - min_v)
+// over the volume Gauss points, c_v = 1 / (2 (2k-1) N_v) (0 if N_v = 0, u_v constant), and per cell
+// sigma^l = max_v c_v A_v(l); the modes of total degree l >= 1 are multiplied by exp(-sigma^l dt).
+__global__ void oedg_filter_kernel(const AuxGeom g, void* st, const OedgOut o, const DevScalars* sc) {
+  volatile OedgScalars* vs = o.sc;
+  if (!vs->active) return;                      // the stage did not run (solve finished or failed)
+  const int lmax = g.dim == 1 ? g.k : (g.basis == 0 ? 2 * g.k : g.k);
+  double cv[4];
+  for (int v = 0; v < g.nv; ++v) {
+    const double avg = vs->sum[v] / (double)g.ncell;
+    const double mx = from_ordered_bits(vs->maxb[v]), mn = from_ordered_bits(~vs->nminb[v]);
+    const double n = fmax(mx - avg, avg - mn);
+    cv[v] = n > 0.0 ? 1.0 / (2.0 * (2 * g.k - 1) * n) : 0.0;
+  }
+  const double dt = ((volatile DevScalars*)sc)->dt;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double fac[7];
+    for (int l = 1; l <= lmax; ++l) {
+      double best = 0.0;
+      for (int v = 0; v < g.nv; ++v) {
+        const long long i = (long long)(v * lmax + l - 1) * g.ncell + c;
+        const double a = g.prec == PREC_F64 ? ((const double*)o.A)[i] : (double)((const float*)o.A)[i];
+        const double sv = cv[v] * a;
+        best = (sv > best || sv != sv) ? sv : best;
+      }
+      fac[l] = exp(-best * dt);
+    }
+    if (g.prec == PREC_F64) {
+      double* b = (double*)st;
+      for (int m = 1; m < g.nm; ++m) {
+        const double f = fac[g.mp[m] + g.mq[m]];
+        for (int v = 0; v < g.nv; ++v) b[((long long)v * g.nm + m) * g.ncell + c] *= f;
+      }
+    } else {
+      float* bh = (float*)((char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+      for (int m = 1; m < g.nm; ++m) {
+        const float f = (float)fac[g.mp[m] + g.mq[m]];
+        for (int v = 0; v < g.nv; ++v) bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c] *= f;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&o.sc->blocks, 1u);
+    if (prev == gridDim.x - 1) {                // every block has read the reductions: clear them
+      for (int v = 0; v < 4; ++v) {
+        vs->sum[v] = 0.0;
+        vs->maxb[v] = 0ull;
+        vs->nminb[v] = 0ull;
+      }
+      vs->active = 0u;
+      vs->blocks = 0u;
+      __threadfence();
+    }
+  }
+}
+
+cudaError_t launch_oedg_filter(const AuxGeom& g, void* state, const OedgOut& o, const DevScalars* sc,
+                               cudaStream_t s) {
+  oedg_filter_kernel<<<1216, 256, 0, s>>>(g, state, o, sc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_storage(const AuxGeom& g, const double* canon, void* state, cudaStream_t s) {
   to_storage_kernel<<<1216, 256, 0, s>>>(g, canon, state);
   return cudaGetLastError();

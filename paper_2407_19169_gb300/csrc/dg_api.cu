@@ -90,8 +90,11 @@ dg_status dgk::validate_config(const dg_mesh* m, int k, int eq, const dg_filter_
   if ((long long)m->nx * (m->dim == 2 ? m->ny : 1) > (1LL << 31)) return DG_ERR_UNSUPPORTED;
   if (p->hybrid && (!p->enabled || p->positivity)) return DG_ERR_UNSUPPORTED;
   if (p->filter_kind < DG_FILTER_JUMP || p->filter_kind > DG_FILTER_OEDG) return DG_ERR_ARG;
-  if (p->filter_kind == DG_FILTER_OEDG) return DG_ERR_UNSUPPORTED;
   if (p->hybrid && p->filter_kind != DG_FILTER_JUMP) return DG_ERR_UNSUPPORTED;
+  // OEDG form: Burgers and Euler, without the positivity limiter (its coefficient needs the whole
+  // stage solution, so the damping runs in a kernel of its own after the stage kernel)
+  if (p->enabled && p->filter_kind == DG_FILTER_OEDG && (p->positivity || eq == DG_EQ_ADVECTION))
+    return DG_ERR_UNSUPPORTED;
   return DG_OK;
 }
 
@@ -139,6 +142,7 @@ void dgk::fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filter
   g.ay = p->adv_speed[1];
   g.pp = (p->positivity && eq == DG_EQ_EULER) ? 1 : 0;
   g.hyb = p->hybrid ? 1 : 0;
+  g.oedg = (p->enabled && p->filter_kind == DG_FILTER_OEDG) ? 1 : 0;
   int idx = 0;
   if (m->dim == 1) {
     for (int l = 0; l <= k; ++l) { g.mp[l] = l; g.mq[l] = 0; }
@@ -156,7 +160,7 @@ void dgk::fill_geom(AuxGeom& g, const dg_mesh* m, int k, int eq, const dg_filter
 // Layout of the single device allocation.
 struct Layout {
   size_t off_buf[3], off_canon, off_part, off_mass, off_sc, off_hy_eta, off_hy_fac, off_hy_list, off_hy_sc,
-      total;
+      off_oe_A, off_oe_sc, total;
 };
 static Layout layout_of(const AuxGeom& g) {
   Layout L;
@@ -181,6 +185,14 @@ static Layout layout_of(const AuxGeom& g) {
     o += align256(sizeof(int) * (size_t)g.ncell);
     L.off_hy_sc = o;
     o += align256(sizeof(HybridScalars));
+  }
+  L.off_oe_A = L.off_oe_sc = 0;
+  if (g.oedg) {
+    const size_t ts = g.prec == PREC_F64 ? sizeof(double) : sizeof(float);
+    L.off_oe_A = o;
+    o += align256(ts * (size_t)g.nv * hybrid_lmax(g) * g.ncell);
+    L.off_oe_sc = o;
+    o += align256(sizeof(OedgScalars));
   }
   L.total = o;
   return L;
@@ -245,7 +257,7 @@ int dgk::default_block_warps(const StageLauncher& L, int max_wpb) {
 
 static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
   if (s->dim == 1) {
-    s->L = stage1d_launcher(s->k, s->eq, s->prec);
+    s->L = stage1d_launcher(s->k, s->eq, s->prec, s->geom.oedg != 0);
     if (!s->L.launch) return DG_ERR_UNSUPPORTED;
     s->nwarps1d = (s->mesh.nx + STRIP_OUT - 1) / STRIP_OUT;
     s->block = 128;
@@ -255,8 +267,9 @@ static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
     s->smem = 256;
     return DG_OK;
   }
-  s->L = s->prec == PREC_F64 ? stage2d_f64_launcher(s->k, s->eq, s->basis)
-                             : stage2d_f32_launcher(s->k, s->eq, s->basis);
+  s->L = s->geom.oedg ? stage2d_oedg_launcher(s->k, s->eq, s->basis, s->prec)
+                      : (s->prec == PREC_F64 ? stage2d_f64_launcher(s->k, s->eq, s->basis)
+                                             : stage2d_f32_launcher(s->k, s->eq, s->basis));
   if (!s->L.launch) return DG_ERR_UNSUPPORTED;
   const int nx = s->mesh.nx, ny = s->mesh.ny;
   s->nstrips = (nx + STRIP_OUT - 1) / STRIP_OUT;
@@ -361,6 +374,11 @@ extern "C" dg_status dg_create(const dg_mesh* mesh, int degree, int equation, in
     s->hy.fac = base + Lo.off_hy_fac;
     s->hy.list = (int*)(base + Lo.off_hy_list);
     s->hy.sc = (HybridScalars*)(base + Lo.off_hy_sc);
+  }
+  s->oe = OedgOut{};
+  if (s->geom.oedg) {
+    s->oe.A = base + Lo.off_oe_A;
+    s->oe.sc = (OedgScalars*)(base + Lo.off_oe_sc);       // zeroed below: empty sums, max and min
   }
   ce = cudaMallocHost(&s->h_sc, sizeof(DevScalars));
   if (ce != cudaSuccess) {
@@ -562,6 +580,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.positivity = s->positivity;
       a.hybrid = s->hybrid;
       a.hyb = s->hy;
+      a.oe = s->oe;
       a.sc = s->sc;
       stage1d_consts(a);
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
@@ -591,6 +610,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.positivity = s->positivity;
       a.hybrid = s->hybrid;
       a.hyb = s->hy;
+      a.oe = s->oe;
       a.sc = s->sc;
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     }
@@ -599,6 +619,12 @@ static cudaError_t launch_step(dg_solver* s, int p) {
     if (s->hybrid) {
       // Algorithm 1: blend the troubled cells once max eta of this stage is known
       e = launch_hybrid_blend(s->geom, dsts[st], s->hy, s->stream);
+      if (e != cudaSuccess) return e;
+      s->launches += 1;
+    }
+    if (s->geom.oedg) {
+      // OEDG: the damping once the stage's normalisers ||u_v - avg u_v||_inf are known
+      e = launch_oedg_filter(s->geom, dsts[st], s->oe, s->sc, s->stream);
       if (e != cudaSuccess) return e;
       s->launches += 1;
     }

@@ -294,7 +294,8 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
   for (int i = 0; i < n; ++i) {
     const dg_solver* s = solvers[i];
     if (!s) return DG_ERR_ARG;
-    if (s->eq != DG_EQ_EULER || s->prec != PREC_F32M || (s->dim == 2 && s->basis != DG_BASIS_Q) || s->hybrid)
+    if (s->eq != DG_EQ_EULER || s->prec != PREC_F32M || (s->dim == 2 && s->basis != DG_BASIS_Q) || s->hybrid ||
+        s->geom.oedg)
       return DG_ERR_UNSUPPORTED;
   }
   if (cudaGetDevice(&dev0) != cudaSuccess) return DG_ERR_CUDA;

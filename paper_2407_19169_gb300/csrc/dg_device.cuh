@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "dg_tables.cuh"
 
@@ -54,6 +55,45 @@ struct HybridOut {
   int* list;                      // [ncell] troubled cells
   HybridScalars* sc;
 };
+
+// OEDG damping (DG_FILTER_OEDG, Section 2.1): the stage kernel stores the unfiltered stage solution
+// and, per output cell, variable v and total degree l, the jump sum A_v(l) of the coefficient
+// (the beta-weighted, h-scaled sums of the edge jumps with the weights (2m+1)/m!); it also reduces,
+// per variable, the sum of the cell averages and the largest and smallest value at the volume Gauss
+// points. The OEDG filter kernel then forms sigma^l = max_v A_v(l) / (2 (2k-1) ||u_v - avg u_v||_inf)
+// and rescales the modes.
+struct OedgScalars {
+  double sum[4];                          // sum of the cell averages per variable
+  unsigned long long maxb[4];             // largest point value per variable (ordered_bits)
+  unsigned long long nminb[4];            // smallest point value per variable (~ordered_bits)
+  unsigned int active;                    // the stage kernel ran (else the filter kernel does nothing)
+  unsigned int blocks;                    // last-block counter of the filter kernel
+};
+struct OedgOut {
+  void* A;                                // [NV][LMAX][ncell], stage arithmetic type
+  OedgScalars* sc;
+};
+// Order-preserving map of a double to 64 bits (atomicMax on signed values); all-zero scalars are
+// the empty max (maxb) and the empty min (nminb).
+__host__ __device__ inline unsigned long long ordered_bits(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof(b));
+#endif
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double from_ordered_bits(unsigned long long o) {
+  const unsigned long long b = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof(x));
+  return x;
+#endif
+}
 
 __host__ __device__ constexpr double cfact(int n) {
   double r = 1.0;

@@ -28,9 +28,10 @@ int default_chunk_rows(const StageLauncher& L, int nstrips, int ny, int wpb, uns
 int default_block_warps(const StageLauncher& L, int max_wpb);
 
 // Instantiation tables (one per kernel file). Return {nullptr} if the combination is not compiled.
-StageLauncher stage1d_launcher(int K, int EQ, int PREC);
+StageLauncher stage1d_launcher(int K, int EQ, int PREC, bool oedg = false);
 StageLauncher stage2d_f64_launcher(int K, int EQ, int BASIS);
 StageLauncher stage2d_f32_launcher(int K, int EQ, int BASIS);
+StageLauncher stage2d_oedg_launcher(int K, int EQ, int BASIS, int PREC);  // OEDG form: Burgers, Euler
 
 // Geometry and physics of one solver, as the auxiliary kernels see it.
 struct AuxGeom {
@@ -40,6 +41,7 @@ struct AuxGeom {
   int mp[16], mq[16];  // (p, q) of each mode
   int pp;              // Euler with the positivity limiter: the CFL rate also takes the limiter's points
   int hyb;             // hybrid limiter (Algorithm 1) scratch in the workspace
+  int oedg;            // OEDG damping: jump sums and reductions in the workspace, filter kernel per stage
 };
 
 cudaError_t aux_init_tables();  // copy Gauss rules to constant memory of the current device
@@ -61,6 +63,10 @@ size_t state_bytes(const AuxGeom& g);
 // omega + (1 - omega) exp(-sigma^l dt), then clear the stage's scalars.
 cudaError_t launch_hybrid_blend(const AuxGeom& g, void* state, const HybridOut& h, cudaStream_t s);
 int hybrid_lmax(const AuxGeom& g);   // highest total degree l of a mode
+// OEDG: sigma^l = max_v A_v(l) / (2 (2k-1) ||u_v - avg u_v||_inf), the modes of `state` rescaled by
+// exp(-sigma^l dt) (dt of the step in progress), then the reductions cleared for the next stage.
+cudaError_t launch_oedg_filter(const AuxGeom& g, void* state, const OedgOut& o, const DevScalars* sc,
+                               cudaStream_t s);
 constexpr int MASS_BLOCKS = 256;
 
 }  // namespace dgk

@@ -65,6 +65,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
   if (vs != DG_OK) return vs;
   if (!u_in || !u_out || u_in == u_out) return DG_ERR_ARG;
   if (p->precision != DG_PREC_FP64 || p->hybrid) return DG_ERR_UNSUPPORTED;
+  if (p->enabled && p->filter_kind == DG_FILTER_OEDG) return DG_ERR_UNSUPPORTED;   // needs scratch of its own
   AuxGeom g;
   fill_geom(g, m, k, eq, p);
   const int dim = m->dim;

@@ -22,6 +22,7 @@ struct dg_solver {
   double* dmass;        // mass result
   dgk::DevScalars* sc;
   dgk::HybridOut hy;    // hybrid limiter scratch (null pointers when off)
+  dgk::OedgOut oe;      // OEDG damping scratch (null pointers when off)
   dgk::DevScalars* h_sc;  // pinned mirror
   long long h_step;     // host's record of the device step count (buffer parity)
   dgk::StageLauncher L;

@@ -34,11 +34,13 @@ struct Stage1DArgs {
   int positivity;    // Euler: Zhang-Shu limiter after the filter
   int hybrid;        // hybrid limiter (Algorithm 1): store u^DG, eta and the filter factors
   HybridOut hyb;
+  OedgOut oe;        // OEDG damping (kernels instantiated with OE = true)
   DevScalars* sc;
   // mesh constants computed once on the host (stage1d_consts): 1/h, 2/h and the jump weights
-  // m(m+1) h^m (1 for m = 0), in both arithmetic types; c0 as a double-float
-  double inv_h_d, scl_d, wpow_d[4];
-  float inv_h_f, scl_f, wpow_f[4];
+  // m(m+1) h^m (1 for m = 0), and the OEDG weights (2m+1)/m! h^m, in both arithmetic types; c0 as
+  // a double-float
+  double inv_h_d, scl_d, wpow_d[4], wpoe_d[4];
+  float inv_h_f, scl_f, wpow_f[4], wpoe_f[4];
   float c0_hi, c0_lo;
 };
 
@@ -49,16 +51,22 @@ inline void stage1d_consts(Stage1DArgs& a) {
   a.inv_h_f = (float)a.inv_h_d;
   a.scl_f = (float)a.scl_d;
   double hp = 1.0;
+  double fm = 1.0;
   for (int m = 0; m < 4; ++m) {
     a.wpow_d[m] = m == 0 ? 1.0 : m * (m + 1) * hp;
     a.wpow_f[m] = (float)a.wpow_d[m];
+    if (m > 0) fm *= m;
+    a.wpoe_d[m] = (2 * m + 1) / fm * hp;
+    a.wpoe_f[m] = (float)a.wpoe_d[m];
     hp *= a.h;
   }
   a.c0_hi = (float)a.c0;
   a.c0_lo = (float)(a.c0 - (double)a.c0_hi);
 }
 
-template <int K, int EQ, class PR>
+// OE = true: the OEDG form of the damping (the kernel stores u~ unfiltered with the jump sums A_v(l)
+// and the reductions of OedgOut; the OEDG filter kernel applies the damping).
+template <int K, int EQ, class PR, bool OE = false>
 struct Stage1D {
   using T = typename PR::T;
   static constexpr int NM = K + 1;
@@ -88,12 +96,21 @@ struct Stage1D {
       inv_h = a.inv_h_f;
       scl = a.scl_f;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) wpow[m] = a.wpow_f[m];
+      for (int m = 0; m < NM; ++m) wpow[m] = OE ? a.wpoe_f[m] : a.wpow_f[m];
     } else {
       inv_h = a.inv_h_d;
       scl = a.scl_d;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) wpow[m] = a.wpow_d[m];
+      for (int m = 0; m < NM; ++m) wpow[m] = OE ? a.wpoe_d[m] : a.wpow_d[m];
+    }
+    constexpr int NVO = OE ? NV : 1;
+    double osum[NVO];
+    T omax[NVO], omin[NVO];
+#pragma unroll
+    for (int v = 0; v < NVO; ++v) {
+      osum[v] = 0.0;
+      omax[v] = -INFINITY;
+      omin[v] = INFINITY;
     }
     const T c1dt = (T)(a.c1 * dtd), c0 = (T)a.c0;
     // double-float coefficients of the cell-average update (once per item, off the cell path)
@@ -285,6 +302,10 @@ struct Stage1D {
           for (int v = 0; v < NV; ++v) {
             run[v] += wpow[l] * J[v][l];
             best = (run[v] > best || run[v] != run[v]) ? run[v] : best;
+            if constexpr (OE) {
+              // A_v(l) = beta / h (J_0 + sum_{m<=l} (2m+1)/m! h^m J_m) for the OEDG filter kernel
+              if (out_lane) ((T*)a.oe.A)[(long long)(v * K + l - 1) * a.ncell + xc] = bx * inv_h * run[v];
+            }
           }
           facs[l] = exp(-(bx * inv_h * invH * best) * dt);
         }
@@ -293,7 +314,23 @@ struct Stage1D {
 #pragma unroll
           for (int l = 1; l < NM - 1; ++l) facs[l] = facs[NM - 1];
         }
-        if (!a.hybrid) {
+        if constexpr (OE) {
+          // u~ is stored as it is; the reductions for the OEDG coefficient
+          if (out_lane) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              osum[v] += (double)ut[v][0] + (double)ulo[v];
+#pragma unroll
+              for (int g = 0; g < NQ; ++g) {
+                T w = T(0);
+#pragma unroll
+                for (int l = 0; l < NM; ++l) w += ut[v][l] * (T)GR::P(l, g);
+                omax[v] = fmax(omax[v], w);
+                omin[v] = fmin(omin[v], w);
+              }
+            }
+          }
+        } else if (!a.hybrid) {
 #pragma unroll
           for (int l = 1; l < NM; ++l)
 #pragma unroll
@@ -326,6 +363,7 @@ struct Stage1D {
       }
     }
     if (a.hybrid) hybrid_max(a.hyb, my_eta);
+    if constexpr (OE) oedg_reduce<NV>(a.oe, osum, omax, omin);
   }
 
   // The limiter's points: the Gauss points, both ends and, for k = 3, the node 0 of the 3-point
@@ -429,6 +467,9 @@ struct Stage1D {
   static __device__ void run(const Stage1DArgs& a, unsigned char* smem) {
     const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
     if (!ctl.run) return;
+    if constexpr (OE) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.oe.sc->active = 1u;
+    }
     double* red = (double*)smem;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nwt = (long long)gridDim.x * (blockDim.x >> 5);
@@ -443,10 +484,10 @@ struct Stage1D {
   }
 };
 
-template <int K, int EQ, class PR>
+template <int K, int EQ, class PR, bool OE = false>
 __global__ void __launch_bounds__(256) stage1d_kernel(const Stage1DArgs a) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  Stage1D<K, EQ, PR>::run(a, dyn_smem);
+  Stage1D<K, EQ, PR, OE>::run(a, dyn_smem);
 }
 
 }  // namespace dgk

@@ -46,6 +46,7 @@ struct Stage2DArgs {
   int positivity;    // Euler: Zhang-Shu limiter after the filter
   int hybrid;        // hybrid limiter (Algorithm 1): store u^DG, eta and the filter factors
   HybridOut hyb;
+  OedgOut oe;        // OEDG damping (kernels instantiated with OE = true)
   DevScalars* sc;
 };
 
@@ -110,7 +111,9 @@ struct Store {
   }
 };
 
-template <int K, int EQ, int BASIS, class PR>
+// OE = true: the OEDG form of the damping (DG_FILTER_OEDG): the kernel stores u~ unfiltered with the
+// jump sums A_v(l) and the reductions of OedgOut, and the OEDG filter kernel applies the damping.
+template <int K, int EQ, int BASIS, class PR, bool OE = false>
 struct Stage2D {
   using T = typename PR::T;
   using MB = Modes<K, BASIS>;
@@ -783,6 +786,30 @@ struct Stage2D {
         hx *= hxT;
         hy *= hyT;
       }
+      if constexpr (OE) {
+        // OEDG: weights (2m+1)/m! h^m, each direction divided by its own h (Section 2.1's form)
+        T hm_x = inv_hx, hm_y = inv_hy;                  // h^(m-1)
+        wx[0] = T(0.5) * inv_hx;
+        wy[0] = T(0.5) * inv_hy;
+#pragma unroll
+        for (int m = 1; m <= LMAX; ++m) {
+          hm_x = m == 1 ? T(1) : hm_x * hxT;
+          hm_y = m == 1 ? T(1) : hm_y * hyT;
+          wx[m] = T(0.5 * (2 * m + 1) / cfact(m)) * hm_x;
+          wy[m] = T(0.5 * (2 * m + 1) / cfact(m)) * hm_y;
+        }
+      }
+    }
+    // OEDG reductions of this lane's output cells: sum of the averages, largest / smallest value at
+    // the volume Gauss points, per variable
+    constexpr int NVO = OE ? NV : 1;
+    double osum[NVO];
+    T omax[NVO], omin[NVO];
+#pragma unroll
+    for (int v = 0; v < NVO; ++v) {
+      osum[v] = 0.0;
+      omax[v] = -INFINITY;
+      omin[v] = INFINITY;
     }
     {
       const int x = strip * STRIP_OUT - 2 + lane;
@@ -1102,6 +1129,8 @@ struct Stage2D {
           }
           avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx1, by1, invH1, phys1);
         }
+        const int ty2 = pery ? ((t - 2) % ny + ny) % ny : t - 2;
+        const long long cell2 = (long long)ty2 * nx + xc;       // the cell filtered in this iteration
         T sig[LMAX + 1];
 #pragma unroll
         for (int l = 0; l <= LMAX; ++l) sig[l] = T(0);
@@ -1175,7 +1204,12 @@ struct Stage2D {
               sfor<GW>([&](auto J_) {
                 constexpr int j = decltype(J_)::value, v = g * GW + j;
                 T* q = wq + ((v * LMAX + (l - 1)) << 5) + lane;
-                if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * comp<j>(shc));   // Q of row t-2 + its top face
+                if constexpr (OE) {
+                  // A_v(l) of row t-2, stored for the OEDG filter kernel
+                  if (filt_row && out_lane) ((T*)a.oe.A)[(long long)(v * LMAX + l - 1) * a.ncell + cell2] = *q + by2 * comp<j>(shc);
+                } else {
+                  if (filt_row) sig[l] = nan_max(sig[l], *q + by2 * comp<j>(shc));   // Q of row t-2 + its top face
+                }
                 if (need_v) *q = bx1 * comp<j>(av) + by1 * comp<j>(shc);          // Q of row t-1 (bottom face)
               });
             }
@@ -1187,8 +1221,6 @@ struct Stage2D {
         }
         if (filt_row) {
           const int s2 = slot_of(t - 2);
-          const int ty2 = pery ? ((t - 2) % ny + ny) % ny : t - 2;
-          const long long cell2 = (long long)ty2 * nx + xc;
           T uo[NV][NM], lo[NV];
           if constexpr (PACK) {
 #pragma unroll
@@ -1212,7 +1244,24 @@ struct Stage2D {
               else lo[v] = T(0);
             }
           }
-          if (a.filter_on) {
+          if constexpr (OE) {
+            // u~ is stored as it is; the reductions for the OEDG coefficient
+            if (out_lane) {
+              auto coef = [](int i, int m) -> double { return lim_coef(i, m); };
+#pragma unroll
+              for (int v = 0; v < NV; ++v) osum[v] += (double)uo[v][0] + (double)lo[v];
+#pragma unroll
+              for (int i = 0; i < NQ * NQ; ++i) {               // the volume Gauss points
+                T w[NV];
+                point_w(uo, i, coef, w);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                  omax[v] = fmax(omax[v], w[v]);
+                  omin[v] = fmin(omin[v], w[v]);
+                }
+              }
+            }
+          } else if (a.filter_on) {
             T fac[LMAX + 1];
 #pragma unroll
             for (int l = 1; l <= LMAX; ++l) fac[l] = exp(-(sig[l] * invH2) * dt);
@@ -1267,6 +1316,7 @@ struct Stage2D {
       }
     }
     if (a.hybrid) hybrid_max(a.hyb, my_eta);
+    if constexpr (OE) oedg_reduce<NV>(a.oe, osum, omax, omin);
   }
 
   // All variables of a cell at limiter point i, w[v] = sum_m coef(i, m) uo[v][m] (the coefficients
@@ -1443,6 +1493,9 @@ struct Stage2D {
   static __device__ void run(const Stage2DArgs& a, unsigned char* smem) {
     const StageCtl ctl = stage_begin(a.sc, a.stage, a.cfl);
     if (!ctl.run) return;
+    if constexpr (OE) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.oe.sc->active = 1u;
+    }
     const int wib = threadIdx.x >> 5;
     double* red = (double*)smem;                                  // 32 doubles for stage_end
     T* ws = (T*)(smem + 256 + warp_bytes() * wib);
@@ -1457,10 +1510,10 @@ struct Stage2D {
   }
 };
 
-template <int K, int EQ, int BASIS, class PR>
+template <int K, int EQ, int BASIS, class PR, bool OE = false>
 __global__ void __launch_bounds__(256) stage2d_kernel(const Stage2DArgs a) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  Stage2D<K, EQ, BASIS, PR>::run(a, dyn_smem);
+  Stage2D<K, EQ, BASIS, PR, OE>::run(a, dyn_smem);
 }
 
 }  // namespace dgk

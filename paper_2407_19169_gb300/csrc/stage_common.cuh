@@ -208,6 +208,28 @@ __device__ __forceinline__ void hybrid_record(const HybridOut& h, long long ncel
   }
 }
 
+// OEDG: the warp's sums of cell averages and its largest / smallest point values into the stage's
+// reductions (called by every lane; lanes without output cells hold 0, -inf, +inf).
+template <int NV, class T>
+__device__ __forceinline__ void oedg_reduce(const OedgOut& o, const double (&sum)[NV], const T (&mx)[NV],
+                                            const T (&mn)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = sum[v], a = (double)mx[v], b = (double)mn[v];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, off);
+      a = fmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+      b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&o.sc->sum[v], s);
+      atomicMax(&o.sc->maxb[v], ordered_bits(a));
+      atomicMax(&o.sc->nminb[v], ~ordered_bits(b));
+    }
+  }
+}
+
 // The warp's largest eta into the stage maximum (called by every lane).
 template <class T>
 __device__ __forceinline__ void hybrid_max(const HybridOut& h, T my_eta) {
