@@ -595,19 +595,23 @@ static void pp_cell(const orc_problem* p, const ctx_t* c, double* u, long cell) 
   double ubar[ORC_MAXNV];
   for (int v = 0; v < c->nv; ++v) ubar[v] = U(u, v, 0, cell);
   const double pbar = orc_pressure(p, ubar);
-  double eps = 1e-10;
+  /* admissibility margins relative to the cell average (the paper gives none): the density at
+   * least eps_r = 1e-3 rho_bar, the pressure at least eps = min(1e-3 (rho_bar + |E_bar|), rho_bar,
+   * p_bar); relative margins keep the velocity at a limited point bounded */
+  const double eps_r = 1e-3 * ubar[0];
+  double eps = 1e-3 * (ubar[0] + fabs(ubar[c->nv - 1]));
   if (ubar[0] < eps) eps = ubar[0];
   if (pbar < eps) eps = pbar;
-  if (!(eps > 0.0)) return;                 /* inadmissible average: reported by the step */
-  /* density: theta_1 = (rho_bar - eps) / (rho_bar - rho_min) when rho_min < eps */
+  if (!(eps > 0.0) || !(eps_r > 0.0)) return;   /* inadmissible average: reported by the step */
+  /* density: theta_1 = (rho_bar - eps_r) / (rho_bar - rho_min) when rho_min < eps_r */
   double rmin = ubar[0];
   for (int i = 0; i < np; ++i) {
     double val[ORC_MAXNV];
     eval_cell(p, c, u, cell, xi[i], eta[i], val);
     if (val[0] < rmin) rmin = val[0];
   }
-  if (rmin < eps) {
-    const double th1 = (ubar[0] - eps) / (ubar[0] - rmin);
+  if (rmin < eps_r) {
+    const double th1 = (ubar[0] - eps_r) / (ubar[0] - rmin);
     for (int m = 1; m < c->nm; ++m) U(u, 0, m, cell) *= th1;
   }
   /* pressure: theta_2 = min over points of t with p(u_bar + t (u(x) - u_bar)) = eps (bisection;

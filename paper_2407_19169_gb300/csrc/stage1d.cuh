@@ -414,12 +414,13 @@ struct Stage1D {
 #pragma unroll
       for (int v = 0; v < NV; ++v) ub[v] = ut[v][0];
       const T pbar = pressure_of<NV>(ub, gm1);
-      // admissibility margins: 1e-10 in FP64 (as the oracle). In the FP32 form point values of rho
-      // and |m|^2 / (2 rho) lose digits to cancellation when rho(x) << rho_bar, so the margins are
-      // relative: rho(x) >= 1e-3 rho_bar and p(x) >= 1e-3 (rho_bar + E_bar), which keeps a limited
-      // point positive when the next stage re-evaluates it in a different order
-      T eps_r = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * ub[0];
-      T eps = sizeof(T) == 8 ? T(1e-10) : T(1e-3) * (ub[0] + fabs(ub[NV - 1]));
+      // admissibility margins, relative to the cell average in both precisions (as the oracle):
+      // rho(x) >= 1e-3 rho_bar and p(x) >= min(1e-3 (rho_bar + |E_bar|), rho_bar, p_bar). Relative
+      // margins keep the velocity at a limited point bounded (an absolute 1e-10 let it grow until
+      // the CFL rate over the limiter's points collapsed dt), and in the FP32 form they keep a
+      // limited point positive when the next stage re-evaluates it in a different order
+      T eps_r = T(1e-3) * ub[0];
+      T eps = T(1e-3) * (ub[0] + fabs(ub[NV - 1]));
       eps_r = ub[0] < eps_r ? ub[0] : eps_r;
       eps = ub[0] < eps ? ub[0] : eps;
       eps = pbar < eps ? pbar : eps;

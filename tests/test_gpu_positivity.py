@@ -53,7 +53,7 @@ def test_lobatto_midline_points_match_oracle(dim, amp):
     # k = 3 cells with rho = 1 + amp P_2(x) (plus a small seeded perturbation) at pressure 1: the
     # density is lowest on the line x = 0, a Gauss-Lobatto mid-line point and not a Gauss point.
     # amp = 1.9: admissible, the largest wave speed (the CFL rate) is there; amp = 2.5: negative
-    # there, limited by the oracle first, so rho(0) = 1e-10 and later stages limit again. A path
+    # there, limited by the oracle first, so rho(0) = 1e-3 rho_bar and later stages limit again. A path
     # without these points takes another dt and differs from the oracle.
     n = 24
     if dim == 1:

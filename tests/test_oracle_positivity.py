@@ -17,8 +17,8 @@ def test_density_scaling_closed_form():
     u[0, :, 0] = [1.0, 1.5]          # rho(-1) = -0.5
     u[2, 0, 0] = 2.5
     out = O.positivity(p, u)
-    eps = 1e-10
-    theta1 = (1.0 - eps) / (1.0 - (-0.5))
+    eps_r = 1e-3 * 1.0                 # the density margin: 1e-3 of the cell average
+    theta1 = (1.0 - eps_r) / (1.0 - (-0.5))
     assert out[0, 1, 0] == pytest.approx(1.5 * theta1, rel=1e-14)
     assert out[0, 0, 0] == u[0, 0, 0] and out[2, 0, 0] == u[2, 0, 0]
 
@@ -27,7 +27,8 @@ def test_density_scaling_closed_form():
 def test_lobatto_midline_points_closed_form(dim):
     # k = 3: rho = 1 + 2.5 P_2(x) is -0.25 at x = 0 but positive at the 4 Gauss nodes (0.18 at
     # +-0.34, 2.3 at +-0.86) and at the ends (3.5). Zhang and Shu's set takes the 3-point
-    # Gauss-Lobatto node 0 as well (2N - 3 >= k), so the limiter acts: theta_1 = (1 - eps) / 1.25.
+    # Gauss-Lobatto node 0 as well (2N - 3 >= k), so the limiter acts: theta_1 = (1 - eps_r) / 1.25
+    # with the density margin eps_r = 1e-3 rho_bar = 1e-3.
     if dim == 1:
         p = O.Problem(dim=1, nx=1, x0=0.0, x1=0.1, k=3, eq=O.EQ_EULER, bc=(O.BC_PERIODIC,) * 4, positivity=1)
     else:
@@ -40,9 +41,9 @@ def test_lobatto_midline_points_closed_form(dim):
     xs, _ = O.gauss(4)
     assert min(1.0 + 2.5 * (1.5 * x * x - 0.5) for x in xs) > 0.0
     out = O.positivity(p, u)
-    theta1 = (1.0 - 1e-10) / 1.25
+    theta1 = (1.0 - 1e-3) / 1.25
     assert out[0, 2, 0] == pytest.approx(2.5 * theta1, rel=1e-14)
-    assert O.evaluate(p, out, 0, 0.0, 0.3)[0] == pytest.approx(1e-10, abs=1e-14)
+    assert O.evaluate(p, out, 0, 0.0, 0.3)[0] == pytest.approx(1e-3, abs=1e-14)
 
 
 def test_pressure_scaling_closed_form():
@@ -51,7 +52,8 @@ def test_pressure_scaling_closed_form():
     u[0, 0, 0] = 1.0
     u[2, :, 0] = [2.5, 3.0]          # E(-1) = -0.5 -> p < 0 at the left end only
     out = O.positivity(p, u)
-    eps = 1e-10
+    # the pressure margin: min(1e-3 (rho_bar + |E_bar|), rho_bar, p_bar) = 1e-3 (1 + 2.5)
+    eps = 1e-3 * 3.5
     # p(u_bar + t d) = 0.4 (2.5 - 3 t) = eps  ->  t = (2.5 - eps / 0.4) / 3
     theta2 = (2.5 - eps / 0.4) / 3.0
     assert out[2, 1, 0] == pytest.approx(3.0 * theta2, rel=1e-12)
@@ -83,13 +85,17 @@ def test_limited_state_is_admissible_and_conservative(dim, k):
         pts = [(a, b) for a in xs for b in xs] + [(s, x) for x in xs for s in lob] + \
             [(x, s) for x in xs for s in lob]
     for c in range(p.ncell):
+        ub = out[:, 0, c]
+        pbar = 0.4 * (ub[-1] - 0.5 * sum(ub[i] ** 2 for i in range(1, len(ub) - 1)) / ub[0])
+        eps_r = 1e-3 * ub[0]                                        # the margins, per cell
+        eps_p = min(1e-3 * (ub[0] + abs(ub[-1])), ub[0], pbar)
         for (xi, eta) in pts:
             val = O.evaluate(p, out, c, xi, eta)
             rho = val[0]
             E = val[-1]
             mom2 = sum(val[i] ** 2 for i in range(1, len(val) - 1))
             pr = 0.4 * (E - 0.5 * mom2 / rho)
-            assert rho >= 1e-10 * (1 - 1e-9) and pr >= 1e-10 - 1e-12
+            assert rho >= eps_r * (1 - 1e-9) and pr >= eps_p * (1 - 1e-9) - 1e-12
 
 
 def test_identity_on_admissible_cells():
