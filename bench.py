@@ -278,6 +278,109 @@ def run_served(N, stream, rate, n_req, budget, policy="srpt", precision=None, si
     return out
 
 
+def _legendre_vander(k, pts):
+    """[l, point] values of P_l, l = 0..k (Bonnet's recurrence)."""
+    import numpy as np
+    V = np.zeros((k + 1, len(pts)))
+    V[0] = 1.0
+    if k >= 1:
+        V[1] = pts
+    for l in range(1, k):
+        V[l + 1] = ((2 * l + 1) * pts * V[l] - l * V[l - 1]) / (l + 1)
+    return V
+
+
+def _l1_vs_finer(uc, nc, uf, nf, k, var, area):
+    """L1 over the domain of (coarse Q^k solution - finer one) for one variable, integrated on the
+    finer mesh's cells at (k+3)^2 Gauss points (the coarse polynomial evaluated there)."""
+    import numpy as np
+    r = nf // nc
+    xg, wg = np.polynomial.legendre.leggauss(k + 3)
+    W = np.outer(wg, wg).ravel() * (area / (nf * nf) / 4.0)
+
+    def vander(pts_x, pts_y):
+        Vx, Vy = _legendre_vander(k, pts_x), _legendre_vander(k, pts_y)
+        return np.stack([np.outer(Vy[q], Vx[p]).ravel() for q in range(k + 1) for p in range(k + 1)])
+
+    Vf = vander(xg, xg)
+    UF = uf[var].reshape(-1, nf, nf)
+    UC = uc[var].reshape(-1, nc, nc)
+    tot = 0.0
+    for b in range(r):
+        for a in range(r):
+            Vc = vander((2 * a + 1 + xg) / r - 1.0, (2 * b + 1 + xg) / r - 1.0)
+            tot += (W[:, None, None] * np.abs(np.einsum("mg,mji->gji", Vc, UC)
+                                              - np.einsum("mg,mji->gji", Vf, UF[:, b::r, a::r]))).sum()
+    return tot
+
+
+def run_accuracy(N, stream):
+    """The error statement of the FP32 form (the kernels of every timed result here), measured
+    against the FP64 path, which matches the FP64 oracle within relative L1 1e-11 in the parity tests:
+    smooth - the isentropic vortex, Q2, 128^2, 100 steps: relative L1 (max over variables at 5x5
+    Gauss points per cell) of FP32 against FP64; shock - the benchmark's problem type (Q2 four-quadrant
+    Riemann data, outflow) at 256^2 to T = 0.05: the L1 error of each path against a 2x finer FP64 run,
+    and their ratio (bar: within 2%)."""
+    import numpy as np
+    from paper_2407_19169_gb300 import inputs as I
+    out = {}
+    # smooth
+    res = {}
+    for prec in (N.PREC_FP64, N.PREC_FP32_MIXED):
+        s = N.Solver(dim=2, nx=128, ny=128, x0=0.0, x1=10.0, y0=-5.0, y1=5.0, bc=(N.BC_PERIODIC,) * 4, k=2,
+                     eq=N.EQ_EULER, precision=prec, stream=stream.cuda_stream)
+        s.set_initial(N.IC_VORTEX2D, [5.0, 0.0, 5.0, 0.0])
+        s.advance_steps(100)
+        st = s.sync()[0]
+        res[prec] = s.read_state()[0] if st == 0 else None
+        s.close()
+    xg, _ = np.polynomial.legendre.leggauss(5)
+    V1 = _legendre_vander(2, xg)
+    V = np.stack([np.outer(V1[q], V1[p]).ravel() for q in range(3) for p in range(3)])
+    a, b = res[N.PREC_FP32_MIXED], res[N.PREC_FP64]
+    worst = max(np.abs(V.T @ (a[v] - b[v])).sum() / np.abs(V.T @ b[v]).sum() for v in range(4))
+    out["smooth"] = {"problem": "isentropic vortex, Q2, 128^2 on [0,10]x[-5,5], 100 steps",
+                     "fp32_vs_fp64_rel_l1": float(worst), "bar": 1e-5}
+    # shock
+    seed = first_accepted_seed()
+    T = 0.05
+    sol = {}
+    for name, prec, n in (("ref", N.PREC_FP64, 512), ("fp64", N.PREC_FP64, 256), ("fp32", N.PREC_FP32_MIXED, 256)):
+        s = N.Solver(dim=2, nx=n, ny=n, bc=(N.BC_OUTFLOW,) * 4, k=2, eq=N.EQ_EULER, precision=prec,
+                     stream=stream.cuda_stream)
+        s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(seed))
+        s.advance_to(T)
+        sol[name] = s.read_state()[0]
+        s.close()
+    e64 = [_l1_vs_finer(sol["fp64"], 256, sol["ref"], 512, 2, v, 1.0) for v in range(4)]
+    e32 = [_l1_vs_finer(sol["fp32"], 256, sol["ref"], 512, 2, v, 1.0) for v in range(4)]
+    ratio = [x / y for x, y in zip(e32, e64)]
+    out["shock"] = {"problem": "four-quadrant Riemann data (seed %d), Q2, 256^2 to T = %g, L1 per variable "
+                               "against a 512^2 FP64 run" % (seed, T),
+                    "l1_fp64": e64, "l1_fp32": e32, "ratio_fp32_over_fp64": ratio,
+                    "max_rel_deviation": max(abs(r - 1.0) for r in ratio), "bar": 0.02}
+    out["reference"] = "the FP64 path, equal to the FP64 oracle within relative L1 1e-11 (tests/test_gpu_parity.py)"
+    return out
+
+
+def run_served_rates(N, stream, args):
+    """S3 at each requested arrival rate (FP32 form; with --served-fp64 also the plain FP64 path on
+    the two smallest sides). Every rate above the measured service rate saturates one GPU, so the
+    latency there is queueing time; `saturation_solves_per_s` is the throughput the GPU sustained."""
+    rates = [float(x) for x in args.served_rates.split(",") if x.strip()]
+    per_rate = []
+    for r in rates:
+        per_rate.append(run_served(N, stream, r, args.served_requests, args.served_budget_gb * 1e9,
+                                   args.served_policy))
+        if args.served_fp64:
+            per_rate.append(run_served(N, stream, r, args.served_requests, args.served_budget_gb * 1e9,
+                                       args.served_policy, precision=N.PREC_FP64, sides=(128, 256)))
+    fp32 = [x for x in per_rate if x.get("precision") == "FP32 form" and x.get("completed")]
+    return {"per_rate": per_rate,
+            "saturation_solves_per_s": max((x["throughput_solves_per_s"] for x in fp32), default=None),
+            "failed_total": sum(x.get("failed", 0) for x in per_rate)}
+
+
 def make_solver(N, precision, nx, seed, stream, tile=(0, 0), hybrid=0):
     from paper_2407_19169_gb300 import inputs as I
     s = N.Solver(dim=2, nx=nx, ny=nx, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(N.BC_OUTFLOW,) * 4, k=2,
@@ -389,10 +492,16 @@ def main():
     ap.add_argument("--batched-tile-rows", type=int, default=0, help="2D tile rows of the batch (0 = autotuned)")
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--skip-small", action="store_true")
+    ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--served-policy", default="srpt", choices=["srpt", "all"],
                     help="which resident solves each round advances (serve.Engine)")
-    ap.add_argument("--served-rate", type=float, default=10.0)
+    ap.add_argument("--served-rates", default="10,500",
+                    help="comma-separated Poisson arrival rates (requests/s), one served run each")
     ap.add_argument("--served-requests", type=int, default=12)
+    ap.add_argument("--served-fp64", action="store_true",
+                    help="also serve the plain FP64 path (sides 128 and 256) at each rate")
+    ap.add_argument("--served-only", action="store_true",
+                    help="run the served sweep alone and print its JSON (no headline line)")
     ap.add_argument("--served-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.mesh == 2048:
@@ -426,6 +535,10 @@ def main():
     seed = first_accepted_seed()
     nx = args.mesh
     out = {}
+    if args.served_only:
+        if rank == 0:
+            print(json.dumps({"served": run_served_rates(N, stream, args)}), flush=True)
+        return
 
     # ---- headline: the FP32 form, inputs resident, autotuned tile shape ----
     tile = (args.tile_rows, args.tile_warps)
@@ -505,9 +618,9 @@ def main():
 
     batched = None if args.skip_batched else run_batched(torch, N, stream, args.batched_steps,
                                                          args.batched_instances, args.batched_tile_rows)
-    served = None if args.skip_served else run_served(N, stream, args.served_rate, args.served_requests,
-                                                      args.served_budget_gb * 1e9, args.served_policy)
+    served = None if args.skip_served else run_served_rates(N, stream, args)
     small = None if args.skip_small else run_small_configs(torch, N, stream, barrier)
+    accuracy = None if args.skip_accuracy else run_accuracy(N, stream)
     if rank != 0:
         return
     line = {
@@ -532,6 +645,7 @@ def main():
         "batched": batched,
         "served": served,
         "small_configs": small,
+        "accuracy": accuracy,
     }
     if not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(128 if nx >= 128 else nx, args.cpu_seconds, seed)

@@ -28,7 +28,7 @@ EXPORTED = ["dg_status_string", "dg_last_error", "dg_params_default", "dg_worksp
             "dg_set_initial", "dg_state_size", "dg_write_state", "dg_write_state_device", "dg_read_state",
             "dg_read_state_device", "dg_step", "dg_advance_to", "dg_advance_steps", "dg_sync", "dg_mass",
             "dg_dims", "dg_kernel_launches", "dg_destroy", "dg_step_noalloc", "dg_set_target",
-            "dg_batch_run"]
+            "dg_batch_run", "dg_probe_fma", "dg_probe_transform"]
 
 
 class Mesh(C.Structure):
@@ -90,6 +90,8 @@ def load():
         "dg_step_noalloc": (I, [P(Mesh), I, I, P(Params), V, V, dp, V]),
         "dg_set_target": (I, [V, D, LL]),
         "dg_batch_run": (I, [P(V), I, LL]),
+        "dg_probe_fma": (I, [I, I, dp]),
+        "dg_probe_transform": (I, [I, LL, I, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

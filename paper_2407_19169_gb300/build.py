@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
 UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "stage2d_oedg.cu", "dg_noalloc.cu",
-         "dg_batch.cu"]
+         "dg_batch.cu", "probes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div=false / -prec-sqrt=false: single-precision division and square root by the hardware
 # approximations (a couple of ulp). They act only on FP32 arithmetic (the FP32 form's stage math);
@@ -32,7 +32,8 @@ def _nvcc() -> str:
 
 def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + \
-        [os.path.join(os.path.dirname(HERE), "include", "dg.h"), os.path.abspath(__file__)]
+        [os.path.join(os.path.dirname(HERE), "include", h) for h in ("dg.h", "dg_probes.h")] + \
+        [os.path.abspath(__file__)]
 
 
 def _stale(obj: str) -> bool:

@@ -1,5 +1,6 @@
 """CPU-only checks of the boundary: the CUDA library builds for sm_103a, loads, exports every entry
-point include/dg.h declares, and the binding's constants equal the header's enums. No kernel runs."""
+point the headers in include/ declare (dg.h, the method; dg_probes.h, the measurement probes), and
+the binding's constants equal the header's enums. No kernel runs."""
 import ctypes
 import os
 import re
@@ -13,10 +14,12 @@ from paper_2407_19169_gb300 import inputs as I
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "dg.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^DG_API\s+[\w\s\*]+?\b(dg_\w+)\s*\(", txt, flags=re.M)))
 
 
@@ -55,6 +58,7 @@ def test_enums_match_header():
     assert val("DG_EQ_EULER") == N.EQ_EULER and val("DG_EQ_BURGERS") == N.EQ_BURGERS
     assert val("DG_BC_OUTFLOW") == N.BC_OUTFLOW and val("DG_PREC_FP32_MIXED") == N.PREC_FP32_MIXED
     assert val("DG_BASIS_P") == N.BASIS_P and val("DG_IC_VORTEX2D") == N.IC_VORTEX2D
+    assert val("DG_FILTER_GLOBAL") == N.FILTER_GLOBAL and val("DG_FILTER_OEDG") == N.FILTER_OEDG
     for code, name in N.STATUS.items():
         assert val(name) == code
 
