@@ -35,7 +35,7 @@ cudaError_t aux_init_tables() {
 
 size_t state_bytes(const AuxGeom& g) {
   if (g.prec == PREC_F64) return sizeof(double) * (size_t)g.nv * g.nm * g.ncell;
-  return (sizeof(float2) + sizeof(float) * (size_t)(g.nm - 1)) * (size_t)g.nv * g.ncell;
+  return F32Layout{g.ncell, g.nv, g.nm}.bytes();
 }
 
 // P_l(x) by the three-term recurrence.
@@ -149,16 +149,16 @@ cudaError_t launch_project(const AuxGeom& g, int ic, const double* prm, int nprm
 // Cell average of variable v from either storage form.
 __device__ inline double avg_of(const AuxGeom& g, const void* st, int v, long long c) {
   if (g.prec == PREC_F64) return ((const double*)st)[((long long)v * g.nm) * g.ncell + c];
-  const float2 a = ((const float2*)st)[(long long)v * g.ncell + c];
-  return (double)a.x + (double)a.y;
+  const F32Layout L{g.ncell, g.nv, g.nm};
+  const float* b = (const float*)st;
+  return (double)b[L.word(v, 0, c)] + (double)b[L.word(v, g.nm, c)];
 }
 
 // Coefficient (v, m) of cell c from either storage form.
 __device__ inline double coef_of(const AuxGeom& g, const void* st, int v, int m, long long c) {
   if (m == 0) return avg_of(g, st, v, c);
   if (g.prec == PREC_F64) return ((const double*)st)[((long long)v * g.nm + m) * g.ncell + c];
-  const float* bh = (const float*)((const char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
-  return (double)bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c];
+  return (double)((const float*)st)[F32Layout{g.ncell, g.nv, g.nm}.word(v, m, c)];
 }
 
 // CFL rate of one state: beta^x / hx (+ beta^y / hy).
@@ -240,8 +240,8 @@ cudaError_t launch_rate(const AuxGeom& g, const void* state, DevScalars* sc, int
 
 __global__ void to_storage_kernel(const AuxGeom g, const double* canon, void* st) {
   const long long total = (long long)g.nv * g.nm * g.ncell;
-  float2* b0 = (float2*)st;
-  float* bh = (float*)((char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+  const F32Layout L{g.ncell, g.nv, g.nm};
+  float* b = (float*)st;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long c = e % g.ncell, vm = e / g.ncell;
@@ -249,26 +249,26 @@ __global__ void to_storage_kernel(const AuxGeom g, const double* canon, void* st
     const double x = canon[e];
     if (m == 0) {
       const float hi = (float)x;
-      b0[(long long)v * g.ncell + c] = make_float2(hi, (float)(x - (double)hi));
+      b[L.word(v, 0, c)] = hi;
+      b[L.word(v, g.nm, c)] = (float)(x - (double)hi);
     } else {
-      bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c] = (float)x;
+      b[L.word(v, m, c)] = (float)x;
     }
   }
 }
 
 __global__ void from_storage_kernel(const AuxGeom g, const void* st, double* canon) {
   const long long total = (long long)g.nv * g.nm * g.ncell;
-  const float2* b0 = (const float2*)st;
-  const float* bh = (const float*)((const char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+  const F32Layout L{g.ncell, g.nv, g.nm};
+  const float* b = (const float*)st;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long c = e % g.ncell, vm = e / g.ncell;
     const int v = (int)(vm / g.nm), m = (int)(vm % g.nm);
     if (m == 0) {
-      const float2 a = b0[(long long)v * g.ncell + c];
-      canon[e] = (double)a.x + (double)a.y;
+      canon[e] = (double)b[L.word(v, 0, c)] + (double)b[L.word(v, g.nm, c)];
     } else {
-      canon[e] = (double)bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c];
+      canon[e] = (double)b[L.word(v, m, c)];
     }
   }
 }
@@ -298,11 +298,12 @@ __global__ void hybrid_blend_kernel(const AuxGeom g, void* st, const HybridOut h
     } else {
       const float e = ((const float*)h.eta)[c];
       const float w = (float)((emax - (double)e) / (emax - 1.0));
-      float* bh = (float*)((char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+      const F32Layout L{g.ncell, g.nv, g.nm};
+      float* b = (float*)st;
       for (int m = 1; m < g.nm; ++m) {
         const int l = g.mp[m] + g.mq[m];
         const float f = w + (1.0f - w) * ((const float*)h.fac)[(long long)(l - 1) * g.ncell + c];
-        for (int v = 0; v < g.nv; ++v) bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c] *= f;
+        for (int v = 0; v < g.nv; ++v) b[L.word(v, m, c)] *= f;
       }
     }
   }
@@ -360,10 +361,11 @@ __global__ void oedg_filter_kernel(const AuxGeom g, void* st, const OedgOut o, c
         for (int v = 0; v < g.nv; ++v) b[((long long)v * g.nm + m) * g.ncell + c] *= f;
       }
     } else {
-      float* bh = (float*)((char*)st + sizeof(float2) * (size_t)g.nv * g.ncell);
+      const F32Layout L{g.ncell, g.nv, g.nm};
+      float* b = (float*)st;
       for (int m = 1; m < g.nm; ++m) {
         const float f = (float)fac[g.mp[m] + g.mq[m]];
-        for (int v = 0; v < g.nv; ++v) bh[((long long)v * (g.nm - 1) + m - 1) * g.ncell + c] *= f;
+        for (int v = 0; v < g.nv; ++v) b[L.word(v, m, c)] *= f;
       }
     }
   }

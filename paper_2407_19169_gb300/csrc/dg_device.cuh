@@ -354,6 +354,41 @@ __device__ __noinline__ T pp_segment(const T* ub, const T* w, T eps, T gm1) {
   return lo;
 }
 
+// ---- storage of the FP32 form ---------------------------------------------------------------
+// Word index (4-byte words from the state's base) of coefficient (v, m) of cell c, m = NM meaning the
+// low word of the double-float cell average.
+//   plain layout (an odd number of variables): float2 planes (hi, lo) of the averages per variable,
+//     then one float plane per (variable, mode >= 1);
+//   paired layout (an even number of variables, 2D Euler): per pair of variables a region of float4
+//     planes over the cells, {hi v0, hi v1, lo v0, lo v1}, then {v0[m], v1[m], v0[m+1], v1[m+1]} for
+//     m = 1, 3, ..., and a float2 plane {v0[m], v1[m]} for a last single mode; each region a multiple
+//     of 16 bytes. A warp reads a pair's two variables, two modes at a time, with 128-bit loads, and
+//     the values land in the register pairs of the packed two-lane FP32 arithmetic.
+struct F32Layout {
+  long long ncell;
+  int nv, nm;
+  __host__ __device__ bool paired() const { return (nv & 1) == 0; }
+  // words of one pair's region
+  __host__ __device__ long long region_words() const { return ((ncell * (4 + 2LL * (nm - 1)) + 3) / 4) * 4; }
+  __host__ __device__ long long word(int v, int m, long long c) const {
+    if (!paired()) {
+      if (m == 0 || m == nm) return 2LL * ((long long)v * ncell + c) + (m == nm ? 1 : 0);
+      return 2LL * nv * ncell + ((long long)v * (nm - 1) + m - 1) * ncell + c;
+    }
+    const long long base = (long long)(v >> 1) * region_words();
+    const int j = v & 1;
+    if (m == 0) return base + 4 * c + j;
+    if (m == nm) return base + 4 * c + 2 + j;
+    const int i = m - 1, q = i >> 1;
+    if (q < (nm - 1) / 2) return base + 4 * ncell * (1 + q) + 4 * c + 2 * (i & 1) + j;
+    return base + 4 * ncell * (1 + (nm - 1) / 2) + 2 * c + j;
+  }
+  __host__ __device__ size_t bytes() const {
+    return paired() ? sizeof(float) * (size_t)(nv / 2) * (size_t)region_words()
+                    : (sizeof(float2) + sizeof(float) * (size_t)(nm - 1)) * (size_t)nv * (size_t)ncell;
+  }
+};
+
 // ---- double-float arithmetic (error-free transformations; Dekker / Knuth) -------------------
 struct df {
   float hi, lo;

@@ -52,8 +52,9 @@ struct Stage2DArgs {
 
 constexpr int STRIP_OUT = 28;  // output columns per warp
 
-// Storage policies. FP64: one double plane per (v, m). FP32 mixed: a float2 (hi, lo) plane per v for
-// the cell average (mode 0, a double-float value), then float planes for modes 1..NM-1.
+// Storage policies. FP64: one double plane per (v, m). FP32 mixed: F32Layout (the cell average of
+// each variable a double-float hi/lo pair; with an even number of variables, pairs of variables in
+// float4 planes).
 struct PrecF64 {
   using T = double;
   static constexpr bool MIXED = false;
@@ -66,6 +67,8 @@ struct PrecF32M {
 template <class PR, int NV, int NM>
 struct Store {
   using T = typename PR::T;
+  // the FP32 form with an even number of variables keeps them in pairs (F32Layout)
+  static constexpr bool PAIRED = PR::MIXED && (NV % 2) == 0;
   // load u[v][m] (and the low word of the mode-0 double-float in lo0[v]).
   static __device__ __forceinline__ void load(const void* base, long long ncell, long long c,
                                               T (&u)[NV][NM], T (&lo0)[NV]) {
@@ -76,6 +79,30 @@ struct Store {
 #pragma unroll
         for (int m = 0; m < NM; ++m) u[v][m] = __ldg(b + (long long)(v * NM + m) * ncell + c);
         lo0[v] = T(0);
+      }
+    } else if constexpr (PAIRED) {
+      const F32Layout L{ncell, NV, NM};
+#pragma unroll
+      for (int pr = 0; pr < NV / 2; ++pr) {
+        const float* r = (const float*)base + pr * L.region_words();
+        const float4 a = __ldg((const float4*)r + c);
+        u[2 * pr][0] = a.x;
+        u[2 * pr + 1][0] = a.y;
+        lo0[2 * pr] = a.z;
+        lo0[2 * pr + 1] = a.w;
+#pragma unroll
+        for (int q = 0; q < (NM - 1) / 2; ++q) {
+          const float4 x = __ldg((const float4*)r + ncell * (1 + q) + c);
+          u[2 * pr][1 + 2 * q] = x.x;
+          u[2 * pr + 1][1 + 2 * q] = x.y;
+          u[2 * pr][2 + 2 * q] = x.z;
+          u[2 * pr + 1][2 + 2 * q] = x.w;
+        }
+        if constexpr (((NM - 1) & 1) != 0) {
+          const float2 y = __ldg((const float2*)(r + 4 * ncell * (1 + (NM - 1) / 2)) + c);
+          u[2 * pr][NM - 1] = y.x;
+          u[2 * pr + 1][NM - 1] = y.y;
+        }
       }
     } else {
       const float2* b0 = (const float2*)base;
@@ -98,6 +125,19 @@ struct Store {
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int m = 0; m < NM; ++m) b[(long long)(v * NM + m) * ncell + c] = u[v][m];
+    } else if constexpr (PAIRED) {
+      const F32Layout L{ncell, NV, NM};
+#pragma unroll
+      for (int pr = 0; pr < NV / 2; ++pr) {
+        float* r = (float*)base + pr * L.region_words();
+        ((float4*)r)[c] = make_float4(u[2 * pr][0], u[2 * pr + 1][0], lo0[2 * pr], lo0[2 * pr + 1]);
+#pragma unroll
+        for (int q = 0; q < (NM - 1) / 2; ++q)
+          ((float4*)r)[ncell * (1 + q) + c] =
+              make_float4(u[2 * pr][1 + 2 * q], u[2 * pr + 1][1 + 2 * q], u[2 * pr][2 + 2 * q], u[2 * pr + 1][2 + 2 * q]);
+        if constexpr (((NM - 1) & 1) != 0)
+          ((float2*)(r + 4 * ncell * (1 + (NM - 1) / 2)))[c] = make_float2(u[2 * pr][NM - 1], u[2 * pr + 1][NM - 1]);
+      }
     } else {
       float2* b0 = (float2*)base;
       float* bh = (float*)((char*)base + sizeof(float2) * (size_t)NV * ncell);
