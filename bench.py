@@ -203,8 +203,13 @@ def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
     from paper_2407_19169_gb300 import tuning
     specs = I.batched_specs(n=n_inst, riemann_seeds=accepted("riemann1d_seeds.txt"),
                             quadrant_seeds=accepted("quadrant_seeds.txt"))
+    # tiles per degree, tuned at the median side of that degree's 2D instances
+    med = {}
+    for k in (1, 2, 3):
+        sides = sorted(sp["n"] for sp in specs if sp["dim"] == 2 and sp["k"] == k)
+        med[k] = sides[len(sides) // 2] if sides else 256
     tiles = ({k: (tile_rows, 4) for k in (1, 2, 3)} if tile_rows else
-             {k: tuning.tune_2d(256, 256, k=k) for k in (1, 2, 3)})
+             {k: tuning.tune_2d(med[k], med[k], k=k) for k in (1, 2, 3)})
     t0 = time.perf_counter()
     inst = [make_instance(N, I, sp, stream.cuda_stream, tiles) for sp in specs]
     setup_s = time.perf_counter() - t0
@@ -227,6 +232,7 @@ def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
     return {"value": work / (ms * 1e-3), "unit": UNIT, "instances": n_inst, "steps_each": steps,
             "total_dofs": int(sum(dofs)), "ms": ms, "failed_instances": int(len(ok) - sum(ok)),
             "status": st, "setup_s": setup_s, "tiles_by_degree": {str(k): list(v) for k, v in tiles.items()},
+            "tuned_at_side": {str(k): v for k, v in med.items()},
             "gpu_launches": launches, "dtype": "f32+df64", "positivity_limiter": True}
 
 

@@ -165,13 +165,14 @@ struct Stage2D {
   static constexpr int NME = NM + (PR::MIXED ? 1 : 0);  // slot words per variable (+ mode-0 low word)
   // FP32 form with an even number of variables: the linear (sum-factorised) parts run on pairs of
   // variables in register pairs (packed FP32 instructions), each lane computing the scalar chain.
-  // The edge traces stay scalar above degree 1: there the pairs cost more register moves than the
-  // packed adds save (measured on GB300, Q2 2048^2: 0.947 ms per stage launch against 1.005 ms).
+  // Edge traces and the double-float cell averages run packed as well at degrees 1-2 (traces) and
+  // 2-3 (averages). Measured on GB300 at 2048^2 Q2 with the paired HBM layout, whose loads land in
+  // the register pairs: 0.788 ms per stage launch scalar, 0.786 with packed traces, 0.798 with packed
+  // averages, 0.764 with both. At degree 1 the packed averages were slower (1024^2: 0.155 -> 0.166
+  // ms), at degree 3 faster (0.851 -> 0.820 ms, traces scalar).
   static constexpr bool PACK = PR::MIXED && (NV % 2) == 0;
-  static constexpr bool PACK_TRACES = PACK && K == 1;
-  // The double-float cell averages run packed at degree 3 only (1024^2: Q3 0.851 -> 0.820 ms; Q2
-  // unchanged; Q1 0.155 -> 0.166 ms, its register count fell from 160 to 128 and the schedule with it).
-  static constexpr bool PACK_DF = PACK && K >= 3;
+  static constexpr bool PACK_TRACES = PACK && K <= 2;
+  static constexpr bool PACK_DF = PACK && K >= 2;
   using GR = GaussRule<NQ>;
   using ST = Store<PR, NV, NM>;
   using TB = Tab2D<K, BASIS>;
