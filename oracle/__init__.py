@@ -38,7 +38,7 @@ class _Problem(C.Structure):
                 ("bc", C.c_int * 4), ("k", C.c_int), ("basis", C.c_int), ("eq", C.c_int),
                 ("gamma", C.c_double), ("adv", C.c_double * 2), ("filter", C.c_int),
                 ("cfl", C.c_double), ("nq", C.c_int), ("filter_dt_mode", C.c_int), ("positivity", C.c_int),
-                ("hybrid", C.c_int), ("filter_kind", C.c_int)]
+                ("hybrid", C.c_int), ("filter_kind", C.c_int), ("filter_study", C.c_int)]
 
 
 @dataclasses.dataclass
@@ -63,6 +63,7 @@ class Problem:
     positivity: int = 0
     hybrid: int = 0
     filter_kind: int = 0
+    filter_study: int = 0
 
     def c(self) -> _Problem:
         s = _Problem()

@@ -73,6 +73,13 @@ typedef struct {
   int positivity;          /* Euler: 1 = Zhang-Shu positivity-preserving limiter after the filter */
   int hybrid;              /* 1 = hybrid limiter of Algorithm 1 (jump filter as the low-order part) */
   int filter_kind;         /* ORC_FILTER_*: the damping coefficients of the filter */
+  int filter_study;        /* 2D jump filter, other readings for a study (0 = the readings in use):
+                              bit 0: beta^x, beta^y as the largest |u|+c, |v|+c over the cell's
+                                     volume and edge Gauss points instead of at the average;
+                              bit 1: Hbar as the cell average of H(u(x)) (volume Gauss rule)
+                                     instead of H of the average state;
+                              bit 2: the max over components taken per direction and the two
+                                     directions added, instead of the max of the sum */
 } orc_problem;
 
 /* ---- basis (orc_basis.c) ---- */

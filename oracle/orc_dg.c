@@ -365,6 +365,32 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
   for (int v = 0; v < c->nv; ++v) ubar[v] = U(u, v, 0, cell);
   double bx = orc_wave_speed(p, 0, ubar), by = orc_wave_speed(p, 1, ubar);
   double Hbar = orc_enthalpy(p, ubar);
+  if (p->filter_study & 3) {
+    /* study readings: wave speeds over the cell's Gauss points, Hbar as the average of H */
+    double hsum = 0.0, wsum = 0.0;
+    for (int a = 0; a < c->nq; ++a)
+      for (int b = 0; b < c->nq; ++b) {
+        double val[ORC_MAXNV];
+        eval_cell(p, c, u, cell, c->xq[a], c->xq[b], val);
+        if (p->filter_study & 1) {
+          bx = fmax(bx, orc_wave_speed(p, 0, val));
+          by = fmax(by, orc_wave_speed(p, 1, val));
+        }
+        hsum += c->wq[a] * c->wq[b] * orc_enthalpy(p, val);
+        wsum += c->wq[a] * c->wq[b];
+      }
+    if (p->filter_study & 1)
+      for (int e = 0; e < 4; ++e)
+        for (int g = 0; g < c->nq; ++g) {
+          const double xi = e < 2 ? (e == 0 ? -1.0 : 1.0) : c->xq[g];
+          const double eta = e < 2 ? c->xq[g] : (e == 2 ? -1.0 : 1.0);
+          double val[ORC_MAXNV];
+          eval_cell(p, c, u, cell, xi, eta, val);
+          bx = fmax(bx, orc_wave_speed(p, 0, val));
+          by = fmax(by, orc_wave_speed(p, 1, val));
+        }
+    if (p->filter_study & 2) Hbar = hsum / wsum;
+  }
   for (int m = 0; m < c->nm; ++m) {
     int pp = c->mp[m], qq = c->mq[m], l = pp + qq;
     if (l == 0) { sig[m] = 0.0; continue; }
@@ -400,7 +426,7 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
     double lam = pp * (pp + 1) + qq * (qq + 1);      /* lambda_{p,q} */
     double cfx = hy * bx / (4.0 * lam * Hbar);       /* c_{f,x}^{p,q} */
     double cfy = hx * by / (4.0 * lam * Hbar);       /* c_{f,y}^{p,q} */
-    double best = 0.0;
+    double best = 0.0, bestx = 0.0, besty = 0.0;
     for (int v = 0; v < c->nv; ++v) {
       double sx = hx * JV[v][0][0], sy = hy * JH[v][0][0];
       for (int mm = 1; mm <= top; ++mm) {
@@ -415,6 +441,12 @@ static void sigma_2d(const orc_problem* p, const ctx_t* c, const double* u, long
         sy += mm * (mm + 1) * pow(hy, mm + 1) * th;
       }
       double s = cfx * sx + cfy * sy;                /* sigma_{i,j,l}(u^(v)) */
+      if (p->filter_study & 4) {                     /* study: per-direction maxima, then added */
+        if (cfx * sx > bestx || isnan(sx)) bestx = cfx * sx;
+        if (cfy * sy > besty || isnan(sy)) besty = cfy * sy;
+        best = bestx + besty;
+        continue;
+      }
       if (s > best || isnan(s)) best = s;
     }
     sig[m] = best * (2.0 / hx) * (2.0 / hy) * lam;
