@@ -612,6 +612,7 @@ static cudaError_t launch_step(dg_solver* s, int p) {
       a.hyb = s->hy;
       a.oe = s->oe;
       a.sc = s->sc;
+      stage2d_consts(a);
       e = s->L.launch(&a, s->grid, s->block, s->smem, s->stream);
     }
     if (e != cudaSuccess) return e;

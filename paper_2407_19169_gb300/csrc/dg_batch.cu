@@ -32,6 +32,9 @@ struct BatchInst {
   // 1D mesh constants from the host (stage1d_consts)
   double inv_h_d, scl_d, wpow_d[4];
   float inv_h_f, scl_f, wpow_f[4];
+  // 2D mesh constants from the host (stage2d_consts)
+  Consts2D<float> cf;
+  Consts2D<double> cd;
 };
 
 struct BatchArgs {
@@ -120,6 +123,8 @@ __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
     a.hybrid = 0;
     a.hyb = HybridOut{};
     a.sc = I.sc;
+    a.cf = I.cf;
+    a.cd = I.cd;
     const long long local = w - I.item0;
     double r = 0.0;
     T rt = T(0);
@@ -338,6 +343,18 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
       I.ax = s->ax;
       I.ay = s->ay;
       I.cfl = s->cfl;
+      if (s->dim == 2) {
+        Stage2DArgs t{};
+        t.hx = s->geom.hx;
+        t.hy = s->geom.hy;
+        t.gamma = s->gamma;
+        t.ax = s->ax;
+        t.ay = s->ay;
+        t.filter_on = s->filter_on;
+        stage2d_consts(t);
+        I.cf = t.cf;
+        I.cd = t.cd;
+      }
       {
         Stage1DArgs t{};
         t.h = s->geom.hx;

@@ -219,7 +219,7 @@ __device__ __forceinline__ void flux2d(const T* u, T* f, T gm1, T ax, T ay) {
     T vx = u[1] * inv, vy = u[2] * inv;
     T p = gm1 * (u[3] - T(0.5) * (u[1] * vx + u[2] * vy));
     T vn = DIR == 0 ? vx : vy;
-    f[0] = u[0] * vn;
+    f[0] = DIR == 0 ? u[1] : u[2];                 // rho u_n is the momentum component itself
     f[1] = u[1] * vn + (DIR == 0 ? p : T(0));
     f[2] = u[2] * vn + (DIR == 1 ? p : T(0));
     f[3] = vn * (u[3] + p);

@@ -168,6 +168,7 @@ extern "C" dg_status dg_step_noalloc(const dg_mesh* m, int k, int eq, const dg_f
       a.hybrid = 0;
       a.hyb = HybridOut{};
       a.sc = sc;
+      stage2d_consts(a);
       if (L.launch(&a, (unsigned)((nw + wpb - 1) / wpb), 32 * wpb, smem, st) != cudaSuccess) return DG_ERR_CUDA;
     }
   }

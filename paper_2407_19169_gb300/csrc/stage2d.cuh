@@ -29,6 +29,18 @@
 
 namespace dgk {
 
+// Mesh and physics constants of a 2D stage, computed once by stage2d_consts (on the host for a
+// single solve, so that the kernel reads them from its parameter space instead of holding them in
+// registers): powers of 2/h for physical derivatives, the filter's per-order jump weights (the jump
+// filter's m(m+1) h^m, or the OEDG form's (2m+1)/m! h^(m-1), with the trapezoid's 1/2), 1/h, gamma,
+// gamma - 1 and the advection velocity.
+template <class T>
+struct Consts2D {
+  T px[4], py[4], wx[7], wy[7];
+  T pxy[16], pxy2[16];   // (2/h_x)^a1 (2/h_y)^a2 at [a1 * 4 + a2], and twice that
+  T ihx, ihy, gam, gm1, ax, ay;
+};
+
 struct Stage2DArgs {
   const void* uin;   // u^(s), the stage input
   const void* un;    // u^n
@@ -48,7 +60,54 @@ struct Stage2DArgs {
   HybridOut hyb;
   OedgOut oe;        // OEDG damping (kernels instantiated with OE = true)
   DevScalars* sc;
+  Consts2D<float> cf;  // stage2d_consts
+  Consts2D<double> cd;
 };
+
+template <class T>
+__host__ __device__ inline void consts2d_fill(Consts2D<T>& c, double hx, double hy, double gamma, double ax,
+                                              double ay, bool oedg) {
+  c.ihx = (T)(1.0 / hx);
+  c.ihy = (T)(1.0 / hy);
+  c.gam = (T)gamma;
+  c.gm1 = (T)(gamma - 1.0);
+  c.ax = (T)ax;
+  c.ay = (T)ay;
+  double px[4], py[4];
+  px[0] = py[0] = 1.0;
+  for (int r = 1; r < 4; ++r) {
+    px[r] = px[r - 1] * (2.0 / hx);
+    py[r] = py[r - 1] * (2.0 / hy);
+  }
+  for (int r = 0; r < 4; ++r) {
+    c.px[r] = (T)px[r];
+    c.py[r] = (T)py[r];
+  }
+  for (int a1 = 0; a1 < 4; ++a1)
+    for (int a2 = 0; a2 < 4; ++a2) {
+      c.pxy[a1 * 4 + a2] = (T)(px[a1] * py[a2]);
+      c.pxy2[a1 * 4 + a2] = (T)(2.0 * px[a1] * py[a2]);
+    }
+  double hmx = 1.0, hmy = 1.0, fm = 1.0;        // h^m, m!
+  for (int m = 0; m < 7; ++m) {
+    if (m > 0) fm *= m;
+    if (!oedg) {
+      c.wx[m] = (T)(m == 0 ? 0.5 : 0.5 * m * (m + 1) * hmx);
+      c.wy[m] = (T)(m == 0 ? 0.5 : 0.5 * m * (m + 1) * hmy);
+    } else {
+      c.wx[m] = (T)(0.5 * (2 * m + 1) / fm * hmx / hx);
+      c.wy[m] = (T)(0.5 * (2 * m + 1) / fm * hmy / hy);
+    }
+    hmx *= hx;
+    hmy *= hy;
+  }
+}
+// Fill a.cf and a.cd from a.hx, a.hy, a.gamma, a.ax, a.ay and the filter kind.
+__host__ __device__ inline void stage2d_consts(Stage2DArgs& a) {
+  const bool oedg = a.filter_on == FILT_OEDG;
+  consts2d_fill(a.cf, a.hx, a.hy, a.gamma, a.ax, a.ay, oedg);
+  consts2d_fill(a.cd, a.hx, a.hy, a.gamma, a.ax, a.ay, oedg);
+}
 
 constexpr int STRIP_OUT = 28;  // output columns per warp
 
@@ -295,6 +354,10 @@ struct Stage2D {
     if constexpr (PACK) return J == 0 ? x.x : x.y;
     else return x;
   }
+  static __device__ __forceinline__ const Consts2D<T>& consts_of(const Stage2DArgs& a) {
+    if constexpr (PR::MIXED) return a.cf;
+    else return a.cd;
+  }
   static __device__ __forceinline__ T shfl_down_t(T x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ T shfl_up_t(T x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
 
@@ -361,6 +424,23 @@ struct Stage2D {
       }
       M[l] = acc;
     });
+  }
+
+  // LLF flux at one face point, 1/2 (f(uL) + f(uR)) - 1/2 alpha (uR - uL), alpha the larger spectral
+  // radius, with the combination on pairs of variables (packed form): fh[vp] = {fh_2vp, fh_2vp+1}.
+  template <int DIR>
+  static __device__ __forceinline__ void llf_pairs(const T (&uL)[NV], const T (&uR)[NV], f2 (&fh)[NV / 2], T gam,
+                                                   T gm1, T ax, T ay) {
+    T fL[NV], fR[NV];
+    flux2d<EQ, DIR>(uL, fL, gm1, ax, ay);
+    flux2d<EQ, DIR>(uR, fR, gm1, ax, ay);
+    const T ha = T(-0.5) * nan_max(speed2d<EQ, DIR>(uL, gam, gm1, ax, ay), speed2d<EQ, DIR>(uR, gam, gm1, ax, ay));
+#pragma unroll
+    for (int vp = 0; vp < NV / 2; ++vp) {
+      const f2 sum = f2{fL[2 * vp], fL[2 * vp + 1]} + f2{fR[2 * vp], fR[2 * vp + 1]};
+      const f2 dif = f2{uR[2 * vp], uR[2 * vp + 1]} - f2{uL[2 * vp], uL[2 * vp + 1]};
+      fh[vp] = vfma(dif, f2{ha, ha}, vscale(sum, T(0.5)));
+    }
   }
 
   // Traces of u on the vertical edges xi = -1 (tl) and xi = +1 (tr) at the edge Gauss points:
@@ -712,7 +792,8 @@ struct Stage2D {
   // |value at +1| + |value at -1| of the R-th derivative of the jump polynomial with coefficients
   // c[0..K] of normal order NO across an x-edge (DIR = 0) or a y-edge (DIR = 1), times f, into acc.
   template <int DIR, int NO, int R, class VT>
-  static __device__ __forceinline__ void corner_pair(const VT (&c)[K + 1], typename vtraits<VT>::S f, VT& acc) {
+  static __device__ __forceinline__ void corner_pair(const VT (&c)[K + 1], typename vtraits<VT>::S f,
+                                                     typename vtraits<VT>::S f2x, VT& acc) {
     using S = typename vtraits<VT>::S;
     constexpr bool HE = DIR == 0 ? xt(NO, R, 0) : yt(NO, R, 0);
     constexpr bool HO = DIR == 0 ? xt(NO, R, 1) : yt(NO, R, 1);
@@ -729,17 +810,17 @@ struct Stage2D {
     if constexpr (HE && HO) {
       acc = vmad(vabs(ev + od) + vabs(ev - od), f, acc);
     } else if constexpr (HE) {
-      acc = vmad(vabs(ev), f + f, acc);      // the same magnitude at both corners
+      acc = vmad(vabs(ev), f2x, acc);        // the same magnitude at both corners
     } else if constexpr (HO) {
-      acc = vmad(vabs(od), f + f, acc);
+      acc = vmad(vabs(od), f2x, acc);
     }
   }
 
   // Right vertical edge of the cell w: per total order m, sum over |alpha| = m of
   // f_alpha (|jump at the bottom corner| + |jump at the top corner|) into sv[m].
   template <class VT>
-  static __device__ __forceinline__ void vertical_jumps(const VT (&w)[NM], VT (&sv)[LMAX + 1], const T (&px)[K + 1],
-                                                        const T (&py)[K + 1]) {
+  static __device__ __forceinline__ void vertical_jumps(const VT (&w)[NM], VT (&sv)[LMAX + 1], const T* pxy,
+                                                        const T* pxy2) {
     sfor<K + 1>([&](auto A1_) {
       constexpr int a1 = decltype(A1_)::value;
       VT W[K + 1];
@@ -754,7 +835,7 @@ struct Stage2D {
       sfor<K + 1>([&](auto A2_) {
         constexpr int a2 = decltype(A2_)::value;
         if constexpr (TB::alpha_ok(a1, a2) && (xt(a1, a2, 0) || xt(a1, a2, 1)))
-          corner_pair<0, a1, a2>(W, px[a1] * py[a2], sv[a1 + a2]);
+          corner_pair<0, a1, a2>(W, pxy[a1 * 4 + a2], pxy2[a1 * 4 + a2], sv[a1 + a2]);
       });
     });
   }
@@ -762,7 +843,7 @@ struct Stage2D {
   // The horizontal edge between the cell below (wb, its top) and the cell above (wa, its bottom).
   template <class VT>
   static __device__ __forceinline__ void horizontal_jumps(const VT (&wa)[NM], const VT (&wb)[NM], VT (&sh)[LMAX + 1],
-                                                          const T (&px)[K + 1], const T (&py)[K + 1]) {
+                                                          const T* pxy, const T* pxy2) {
     sfor<K + 1>([&](auto A2_) {
       constexpr int a2 = decltype(A2_)::value;
       VT V[K + 1];
@@ -778,7 +859,7 @@ struct Stage2D {
       sfor<K + 1>([&](auto A1_) {
         constexpr int a1 = decltype(A1_)::value;
         if constexpr (TB::alpha_ok(a1, a2) && (yt(a2, a1, 0) || yt(a2, a1, 1)))
-          corner_pair<1, a2, a1>(V, px[a1] * py[a2], sh[a1 + a2]);
+          corner_pair<1, a2, a1>(V, pxy[a1 * 4 + a2], pxy2[a1 * 4 + a2], sh[a1 + a2]);
       });
     });
   }
@@ -798,49 +879,24 @@ struct Stage2D {
     T* weta = wq + NV * LMAX * 32;                                // hybrid: eta of the next row, partial
     T my_eta = T(0);
     const int nx = a.nx, ny = a.ny;
-    const T gam = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), ax = (T)a.ax, ay = (T)a.ay;
+    // mesh and physics constants from the kernel parameters (stage2d_consts)
+    const Consts2D<T>& KC = consts_of(a);
+    const T gam = KC.gam, gm1 = KC.gm1, ax = KC.ax, ay = KC.ay;
     const double ihx = 1.0 / a.hx, ihy = 1.0 / a.hy, c1dt = a.c1 * dtd;
-    const T inv_hx = (T)ihx, inv_hy = (T)ihy;
+    const T inv_hx = KC.ihx, inv_hy = KC.ihy;
     // u~ = u + c0 (u^n - u) + c1 dt R: the edge and volume integrals enter through c1 dt / h
     const T sx = (T)(c1dt * ihx), sy = (T)(c1dt * ihy), c0 = (T)a.c0;
     // double-float coefficients of the cell-average update (computed once, off the cell loop)
     const df dfx = df_from_double(0.5 * c1dt * ihx);
     const df dfy = df_from_double(0.5 * c1dt * ihy);
     const df dfc0 = df_from_double(a.c0);
-    // powers of 2/h for physical derivatives; weights m(m+1) h^m of the m-th derivative jumps, with
-    // the 1/2 of the trapezoidal rule over an edge's two corners
-    T px[K + 1], py[K + 1], wx[LMAX + 1], wy[LMAX + 1];
-    {
-      const T hxT = (T)a.hx, hyT = (T)a.hy, tx = T(2) * inv_hx, ty = T(2) * inv_hy;
-      px[0] = py[0] = T(1);
-#pragma unroll
-      for (int r = 1; r <= K; ++r) {
-        px[r] = px[r - 1] * tx;
-        py[r] = py[r - 1] * ty;
-      }
-      T hx = hxT, hy = hyT;
-      wx[0] = wy[0] = T(0.5);
-#pragma unroll
-      for (int m = 1; m <= LMAX; ++m) {
-        wx[m] = T(0.5 * m * (m + 1)) * hx;
-        wy[m] = T(0.5 * m * (m + 1)) * hy;
-        hx *= hxT;
-        hy *= hyT;
-      }
-      if constexpr (OE) {
-        // OEDG: weights (2m+1)/m! h^m, each direction divided by its own h (Section 2.1's form)
-        T hm_x = inv_hx, hm_y = inv_hy;                  // h^(m-1)
-        wx[0] = T(0.5) * inv_hx;
-        wy[0] = T(0.5) * inv_hy;
-#pragma unroll
-        for (int m = 1; m <= LMAX; ++m) {
-          hm_x = m == 1 ? T(1) : hm_x * hxT;
-          hm_y = m == 1 ? T(1) : hm_y * hyT;
-          wx[m] = T(0.5 * (2 * m + 1) / cfact(m)) * hm_x;
-          wy[m] = T(0.5 * (2 * m + 1) / cfact(m)) * hm_y;
-        }
-      }
-    }
+    // powers of 2/h for physical derivatives; weights of the m-th derivative jumps (with the 1/2 of
+    // the trapezoidal rule over an edge's two corners): the jump filter's m(m+1) h^m, or the OEDG
+    // form's (2m+1)/m! h^m, each direction divided by its own h (Section 2.1's form)
+    const T* px = KC.px;
+    const T* py = KC.py;
+    const T* wx = KC.wx;
+    const T* wy = KC.wy;
     // OEDG reductions of this lane's output cells: sum of the averages, largest / smallest value at
     // the volume Gauss points, per variable
     constexpr int NVO = OE ? NV : 1;
@@ -895,15 +951,15 @@ struct Stage2D {
           T bot[NQ][NV], top[NQ][NV];
           edge_traces_h(u, bot, top);
           if (t >= yb - 1) {
-            T Fh[NQ][NV];
-#pragma unroll
-            for (int g = 0; g < NQ; ++g) llf2d<EQ, 1>(topPrev[g], bot[g], Fh[g], gam, gm1, ax, ay);
             if constexpr (PACK) {
+              f2 Fh2[NQ][NV / 2];
+#pragma unroll
+              for (int g = 0; g < NQ; ++g) llf_pairs<1>(topPrev[g], bot[g], Fh2[g], gam, gm1, ax, ay);
 #pragma unroll
               for (int vp = 0; vp < NV / 2; ++vp) {
                 f2 F[NQ], M[K + 1];
 #pragma unroll
-                for (int g = 0; g < NQ; ++g) F[g] = f2{Fh[g][2 * vp], Fh[g][2 * vp + 1]};
+                for (int g = 0; g < NQ; ++g) F[g] = Fh2[g][vp];
                 gauss_moments<0>(F, M);
 #pragma unroll
                 for (int p = 0; p <= K; ++p) {
@@ -912,6 +968,9 @@ struct Stage2D {
                 }
               }
             } else {
+              T Fh[NQ][NV];
+#pragma unroll
+              for (int g = 0; g < NQ; ++g) llf2d<EQ, 1>(topPrev[g], bot[g], Fh[g], gam, gm1, ax, ay);
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
                 T F[NQ];
@@ -983,26 +1042,27 @@ struct Stage2D {
           // vertical faces: F^ at xi = +1 by this lane, the one at xi = -1 from the left lane
           T MR[NV][K + 1], ML[NV][K + 1];
           {
-            T tl[NQ][NV], tr[NQ][NV], FR[NQ][NV], FL[NQ][NV];
+            T tl[NQ][NV], tr[NQ][NV];
             edge_traces_v(u, tl, tr);
-#pragma unroll
-            for (int g = 0; g < NQ; ++g) {
-              T nb[NV];
-#pragma unroll
-              for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[g][v], 1);
-              llf2d<EQ, 0>(tr[g], nb, FR[g], gam, gm1, ax, ay);
-#pragma unroll
-              for (int v = 0; v < NV; ++v) FL[g][v] = shfl_up_t(FR[g][v], 1);
-            }
             if constexpr (PACK) {
+              f2 FR2[NQ][NV / 2], FL2[NQ][NV / 2];
+#pragma unroll
+              for (int g = 0; g < NQ; ++g) {
+                T nb[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[g][v], 1);
+                llf_pairs<0>(tr[g], nb, FR2[g], gam, gm1, ax, ay);
+#pragma unroll
+                for (int vp = 0; vp < NV / 2; ++vp) FL2[g][vp] = shfl_up_v(FR2[g][vp], 1);
+              }
 #pragma unroll
               for (int vp = 0; vp < NV / 2; ++vp) {
                 const int v0 = 2 * vp, v1 = v0 + 1;
                 f2 FRv[NQ], FLv[NQ], MRp[K + 1], MLp[K + 1];
 #pragma unroll
                 for (int g = 0; g < NQ; ++g) {
-                  FRv[g] = f2{FR[g][v0], FR[g][v1]};
-                  FLv[g] = f2{FL[g][v0], FL[g][v1]};
+                  FRv[g] = FR2[g][vp];
+                  FLv[g] = FL2[g][vp];
                 }
                 gauss_moments<0>(FRv, MRp);
                 gauss_moments<0>(FLv, MLp);
@@ -1015,6 +1075,16 @@ struct Stage2D {
                 }
               }
             } else {
+              T FR[NQ][NV], FL[NQ][NV];
+#pragma unroll
+              for (int g = 0; g < NQ; ++g) {
+                T nb[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) nb[v] = shfl_down_t(tl[g][v], 1);
+                llf2d<EQ, 0>(tr[g], nb, FR[g], gam, gm1, ax, ay);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) FL[g][v] = shfl_up_t(FR[g][v], 1);
+              }
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
                 T FRv[NQ], FLv[NQ];
@@ -1227,8 +1297,8 @@ struct Stage2D {
             VG sv[LMAX + 1], sh[LMAX + 1];
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) sv[l] = sh[l] = z;
-            if (need_v) vertical_jumps(w1, sv, px, py);
-            horizontal_jumps(w1, w2, sh, px, py);
+            if (need_v) vertical_jumps(w1, sv, KC.pxy, KC.pxy2);
+            horizontal_jumps(w1, w2, sh, KC.pxy, KC.pxy2);
             VG av = z, shc = z;
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) {
@@ -1315,6 +1385,15 @@ struct Stage2D {
               // u^DG is stored as it is; the blend kernel limits the troubled cells
               hybrid_record<T, LMAX>(a.hyb, a.ncell, cell2, out_lane, eta2, fac);
               if (out_lane) my_eta = nan_max(eta2, my_eta);
+            } else if constexpr (PACK) {
+#pragma unroll
+              for (int vp = 0; vp < NV / 2; ++vp)
+#pragma unroll
+                for (int m = 1; m < NM; ++m) {
+                  const f2 r = vscale(f2{uo[2 * vp][m], uo[2 * vp + 1][m]}, fac[PP[m] + QQ[m]]);
+                  uo[2 * vp][m] = r.x;
+                  uo[2 * vp + 1][m] = r.y;
+                }
             } else {
 #pragma unroll
               for (int v = 0; v < NV; ++v)
