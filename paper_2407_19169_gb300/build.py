@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
-UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "stage2d_oedg.cu", "dg_noalloc.cu",
-         "dg_batch.cu", "probes.cu"]
+UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "stage2d_lean.cu", "stage2d_oedg.cu",
+         "dg_noalloc.cu", "dg_batch.cu", "probes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div=false / -prec-sqrt=false: single-precision division and square root by the hardware
 # approximations (a couple of ulp). They act only on FP32 arithmetic (the FP32 form's stage math);

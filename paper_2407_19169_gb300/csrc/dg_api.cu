@@ -267,9 +267,13 @@ static dg_status setup_launch(dg_solver* s, int tile_rows, int tile_warps) {
     s->smem = 256;
     return DG_OK;
   }
+  // the FP32 form of a solve without the positivity and hybrid limiters runs the kernel compiled
+  // without their code (a smaller loop body)
+  const bool lean = s->prec == PREC_F32M && !s->positivity && !s->hybrid;
   s->L = s->geom.oedg ? stage2d_oedg_launcher(s->k, s->eq, s->basis, s->prec)
                       : (s->prec == PREC_F64 ? stage2d_f64_launcher(s->k, s->eq, s->basis)
-                                             : stage2d_f32_launcher(s->k, s->eq, s->basis));
+                                             : (lean ? stage2d_f32_lean_launcher(s->k, s->eq, s->basis)
+                                                     : stage2d_f32_launcher(s->k, s->eq, s->basis)));
   if (!s->L.launch) return DG_ERR_UNSUPPORTED;
   const int nx = s->mesh.nx, ny = s->mesh.ny;
   s->nstrips = (nx + STRIP_OUT - 1) / STRIP_OUT;

@@ -32,6 +32,7 @@ StageLauncher stage1d_launcher(int K, int EQ, int PREC, bool oedg = false);
 StageLauncher stage2d_f64_launcher(int K, int EQ, int BASIS);
 StageLauncher stage2d_f32_launcher(int K, int EQ, int BASIS);
 StageLauncher stage2d_oedg_launcher(int K, int EQ, int BASIS, int PREC);  // OEDG form: Burgers, Euler
+StageLauncher stage2d_f32_lean_launcher(int K, int EQ, int BASIS);         // FP32 form, no limiter code
 
 // Geometry and physics of one solver, as the auxiliary kernels see it.
 struct AuxGeom {
