@@ -13,8 +13,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
-UNITS = ["dg_api.cu", "aux.cu", "stage1d.cu", "stage2d_f64.cu", "stage2d_f32.cu", "stage2d_lean.cu", "stage2d_oedg.cu",
-         "dg_noalloc.cu", "dg_batch.cu", "probes.cu"]
+# (source, object, defines): stage2d_units.cu is compiled once per (form, degree) of the 2D stage
+# kernel and once for its dispatch tables, so that its slow instantiations compile in parallel.
+UNITS = [(u, u.replace(".cu", ".o"), []) for u in
+         ["dg_api.cu", "aux.cu", "stage1d.cu", "dg_noalloc.cu", "dg_batch.cu", "probes.cu"]] + \
+        [("stage2d_units.cu", "stage2d_f%d_k%d.o" % (f, k), ["-DS2_FORM=%d" % f, "-DS2_K=%d" % k])
+         for f in range(5) for k in (1, 2, 3)] + \
+        [("stage2d_units.cu", "stage2d_dispatch.o", ["-DS2_DISPATCH"])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div=false / -prec-sqrt=false: single-precision division and square root by the hardware
 # approximations (a couple of ulp). They act only on FP32 arithmetic (the FP32 form's stage math);
@@ -47,13 +52,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     jobs = []
-    for u in UNITS:
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
+    for src, o, defs in UNITS:
+        obj = os.path.join(BUILD, o)
         if force or _stale(obj):
-            cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, u), "-o", obj]
-            jobs.append((u, cmd))
+            cmd = [nvcc] + ARCH + FLAGS + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
+            jobs.append((o, cmd))
     if jobs:
-        with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        # the slowest units first, so that they start before the pool fills
+        jobs.sort(key=lambda j: ("_k3" not in j[0], "_f0" not in j[0] and "_f3" not in j[0]))
+        with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
             futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): u for u, cmd in jobs}
             for f in cf.as_completed(futs):
                 r = f.result()
@@ -61,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     raise RuntimeError("nvcc failed for %s:\n%s" % (futs[f], r.stderr[-4000:]))
                 if verbose and r.stderr:
                     print(r.stderr)
-    objs = [os.path.join(BUILD, u.replace(".cu", ".o")) for u in UNITS]
+    objs = [os.path.join(BUILD, o) for _, o, _ in UNITS]
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp.%d" % os.getpid()
         subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])

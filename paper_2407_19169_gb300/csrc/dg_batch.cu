@@ -5,7 +5,8 @@
 // Instances of one (dimension, degree) class share one grid-stride work-list kernel per stage: a
 // warp takes the next item of the class, finds its instance by binary search over the instances'
 // first-item offsets, and runs the same item() body as the single-solve kernel with that instance's
-// dt and buffers. Large and small instances therefore share the GPU in proportion to their work.
+// dt and buffers. 2D classes are split by the positivity limiter, so that every instance runs the
+// instantiation it runs alone (the one without the limiter code when the limiter is off). Large and small instances therefore share the GPU in proportion to their work.
 //
 // Step control per instance, without inter-block waits: a begin kernel computes each instance's
 // dt from its CFL rate max (clipped to its T_end), the three stage launches follow, and an end
@@ -65,9 +66,11 @@ __device__ __forceinline__ void item_end(const BatchInst& I, int stage, long lon
   __syncwarp();
 }
 
-template <int K, int EQ, int B, class PR>
+// LIM = false: the instantiation without the limiter code, the one a solve without the positivity
+// limiter runs alone, so that its batched results equal its solo results bit for bit.
+template <int K, int EQ, int B, class PR, bool LIM>
 __global__ void __launch_bounds__(256) batch2d_kernel(const BatchArgs b) {
-  using S = Stage2D<K, EQ, B, PR>;
+  using S = Stage2D<K, EQ, B, PR, false, LIM>;
   using T = typename PR::T;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int wib = threadIdx.x >> 5;
@@ -247,23 +250,28 @@ struct BatchLauncher {
   int (*blocks_per_sm)(unsigned block, size_t smem);  // 2D: resident blocks per SM
 };
 
-template <int K>
+template <int K, bool LIM>
 static cudaError_t launch_b2(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
-  batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M><<<g, bl, sm, s>>>(b);
+  batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M, LIM><<<g, bl, sm, s>>>(b);
   return cudaGetLastError();
 }
-template <int K>
+template <int K, bool LIM>
 static cudaError_t smem_b2(size_t bytes) {
-  return cudaFuncSetAttribute(batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M>,
+  return cudaFuncSetAttribute(batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M, LIM>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-template <int K>
+template <int K, bool LIM>
 static int occ_b2(unsigned block, size_t smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M>, (int)block,
-                                                    smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M, LIM>,
+                                                    (int)block, smem) != cudaSuccess)
     return 0;
   return n;
+}
+template <int K, bool LIM>
+static BatchLauncher make_b2() {
+  return {&launch_b2<K, LIM>, &smem_b2<K, LIM>, Stage2D<K, EQ_EULER, BASIS_Q, PrecF32M, false, LIM>::warp_bytes(),
+          &occ_b2<K, LIM>};
 }
 template <int K>
 static cudaError_t launch_b1(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
@@ -272,12 +280,13 @@ static cudaError_t launch_b1(const BatchArgs& b, unsigned g, unsigned bl, size_t
 }
 static cudaError_t smem_none(size_t) { return cudaSuccess; }
 
-static BatchLauncher batch_launcher(int dim, int K) {
+// lim: the 2D instantiation with the limiter code (classes of solves with the positivity limiter)
+static BatchLauncher batch_launcher(int dim, int K, bool lim) {
   if (dim == 2) {
     switch (K) {
-      case 1: return {&launch_b2<1>, &smem_b2<1>, Stage2D<1, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes(), &occ_b2<1>};
-      case 2: return {&launch_b2<2>, &smem_b2<2>, Stage2D<2, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes(), &occ_b2<2>};
-      case 3: return {&launch_b2<3>, &smem_b2<3>, Stage2D<3, EQ_EULER, BASIS_Q, PrecF32M>::warp_bytes(), &occ_b2<3>};
+      case 1: return lim ? make_b2<1, true>() : make_b2<1, false>();
+      case 2: return lim ? make_b2<2, true>() : make_b2<2, false>();
+      case 3: return lim ? make_b2<3, true>() : make_b2<3, false>();
     }
   } else {
     switch (K) {
@@ -308,8 +317,9 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
     if (solver_pull_control(solvers[i]) != DG_OK) return DG_ERR_CUDA;   // also orders prior work
   if (steps == 0) return DG_OK;
 
-  // classes: (dim, K) -> index dim_index * 3 + K - 1
-  constexpr int NCLS = 6;
+  // classes: 1D degree K -> K - 1; 2D degree K without / with the positivity limiter -> 2 + K,
+  // 5 + K (the 2D kernel instantiation a solve runs alone)
+  constexpr int NCLS = 9;
   std::vector<BatchInst> host;
   host.reserve(n);
   int cls_begin[NCLS], cls_count[NCLS], cls_wpb[NCLS];
@@ -318,10 +328,10 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
     cls_begin[c] = (int)host.size();
     cls_items[c] = 0;
     cls_wpb[c] = 4;
-    const int dim = c < 3 ? 1 : 2, K = c % 3 + 1;
+    const int dim = c < 3 ? 1 : 2, K = c % 3 + 1, lim = c >= 6 ? 1 : 0;
     for (int i = 0; i < n; ++i) {
       const dg_solver* s = solvers[i];
-      if (s->dim != dim || s->k != K) continue;
+      if (s->dim != dim || s->k != K || (dim == 2 && s->positivity != lim)) continue;
       BatchInst I;
       memset(&I, 0, sizeof(I));
       for (int b = 0; b < 3; ++b) I.buf[b] = s->buf[b];
@@ -400,7 +410,7 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
   int nsm = 152;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev0) != cudaSuccess || nsm <= 0) nsm = 152;
   for (int c = 0; c < NCLS && e == cudaSuccess; ++c) {
-    BL[c] = batch_launcher(c < 3 ? 1 : 2, c % 3 + 1);
+    BL[c] = batch_launcher(c < 3 ? 1 : 2, c % 3 + 1, c >= 6);
     cls_cap[c] = (long long)nsm * 4;
     if (c >= 3 && cls_count[c] > 0) {
       int maxw = (int)((200 * 1024) / BL[c].warp_bytes);
