@@ -197,8 +197,10 @@ def make_instance(N, I, spec, stream, tiles):
 
 def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
     """S2: n_inst uneven instances (inputs.batched_specs), each advanced `steps` steps by dg_batch_run
-    (one graph-captured work-list launch per class and stage); autotuned 2D tiles per degree; the
-    positivity-preserving limiter after the filter, as the paper does for hard Riemann data."""
+    (one graph-captured work-list launch per class and stage), then the same instances afresh by
+    dg_batch_run_persistent (one persistent launch per class for all steps); autotuned 2D tiles per
+    degree; the positivity-preserving limiter after the filter, as the paper does for hard Riemann
+    data."""
     from paper_2407_19169_gb300 import inputs as I
     from paper_2407_19169_gb300 import tuning
     specs = I.batched_specs(n=n_inst, riemann_seeds=accepted("riemann1d_seeds.txt"),
@@ -210,30 +212,41 @@ def run_batched(torch, N, stream, steps, n_inst, tile_rows=0):
         med[k] = sides[len(sides) // 2] if sides else 256
     tiles = ({k: (tile_rows, 4) for k in (1, 2, 3)} if tile_rows else
              {k: tuning.tune_2d(med[k], med[k], k=k) for k in (1, 2, 3)})
-    t0 = time.perf_counter()
-    inst = [make_instance(N, I, sp, stream.cuda_stream, tiles) for sp in specs]
-    setup_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    dofs = [x.size for x in inst]
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    l0 = inst[0].kernel_launches()
-    e0.record(stream)
-    st = N.batch_run(inst, steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = inst[0].kernel_launches() - l0
-    done = [x.sync() for x in inst]
-    ok = [d[0] == 0 and d[2] == steps for d in done]
-    work = sum(3.0 * d * steps for d, o in zip(dofs, ok) if o)
-    for x in inst:
-        x.close()
-    return {"value": work / (ms * 1e-3), "unit": UNIT, "instances": n_inst, "steps_each": steps,
-            "total_dofs": int(sum(dofs)), "ms": ms, "failed_instances": int(len(ok) - sum(ok)),
-            "status": st, "setup_s": setup_s, "tiles_by_degree": {str(k): list(v) for k, v in tiles.items()},
-            "tuned_at_side": {str(k): v for k, v in med.items()},
-            "gpu_launches": launches, "dtype": "f32+df64", "positivity_limiter": True}
+    def one(persistent):
+        t0 = time.perf_counter()
+        inst = [make_instance(N, I, sp, stream.cuda_stream, tiles) for sp in specs]
+        setup_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        dofs = [x.size for x in inst]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = inst[0].kernel_launches()
+        e0.record(stream)
+        st = N.batch_run(inst, steps, persistent=persistent)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = inst[0].kernel_launches() - l0
+        done = [x.sync() for x in inst]
+        ok = [d[0] == 0 and d[2] == steps for d in done]
+        work = sum(3.0 * d * steps for d, o in zip(dofs, ok) if o)
+        for x in inst:
+            x.close()
+        rec = {"value": work / (ms * 1e-3), "unit": UNIT, "instances": n_inst, "steps_each": steps,
+               "total_dofs": int(sum(dofs)), "ms": ms, "failed_instances": int(len(ok) - sum(ok)),
+               "status": st, "setup_s": setup_s, "gpu_launches": launches, "dtype": "f32+df64",
+               "positivity_limiter": True}
+        return rec, [d[1] for d in done]
+
+    graph, t_graph = one(False)
+    graph["tiles_by_degree"] = {str(k): list(v) for k, v in tiles.items()}
+    graph["tuned_at_side"] = {str(k): v for k, v in med.items()}
+    # the same instances advanced by dg_batch_run_persistent: one cooperative launch per class runs all
+    # steps, per-instance stage barriers on device counters
+    pers, t_pers = one(True)
+    pers["same_end_times_as_graph"] = bool(t_pers == t_graph)
+    graph["persistent"] = pers
+    return graph
 
 
 def run_small_configs(torch, N, stream, barrier):

@@ -46,7 +46,8 @@ typedef enum {
   DG_ERR_OOM = -2,          /* device allocation failed                                        */
   DG_ERR_BUDGET = -3,       /* workspace too small / admission budget exceeded                 */
   DG_ERR_NONPHYSICAL = -4,  /* a cell average became non-finite, rho <= 0 or p <= 0            */
-  DG_ERR_TIMEOUT = -5,      /* advance_to hit max_steps before reaching T                      */
+  DG_ERR_TIMEOUT = -5,      /* advance_to hit max_steps before reaching T; a bounded device wait
+                               of dg_batch_run_persistent gave up                                  */
   DG_ERR_CUDA = -6,         /* a CUDA runtime call failed (message: dg_last_error)             */
   DG_ERR_STATE = -7,        /* call not valid in the solver's current state                    */
   DG_ERR_UNSUPPORTED = -8   /* configuration outside the compiled kernels (see dg_create)      */
@@ -114,8 +115,8 @@ typedef struct {
  *             not depend on them
  *   positivity Euler only: 1 = the positivity-preserving limiter of Zhang and Shu after the filter in
  *             every stage (the paper applies it this way in Section 3.2), 0 = off (default): density
- *             and pressure are kept >= min(1e-10, rho_bar, p_bar) (FP64; the FP32 form keeps them
- *             >= 1e-3 rho_bar and 1e-3 (rho_bar + |E_bar|)) at the volume and edge Gauss points and,
+ *             is kept >= 1e-3 rho_bar and pressure >= min(1e-3 (rho_bar + |E_bar|), rho_bar, p_bar)
+ *             (both precisions; the paper gives no margin) at the volume and edge Gauss points and,
  *             at degree 3, the Gauss-Lobatto mid-lines, by scaling the modes l >= 1; cell averages
  *             are untouched; the CFL rate then includes the wave speeds at those points
  *   hybrid    1 = the hybrid limiter of Algorithm 1 (Section 2.4) after every stage instead of the
@@ -209,6 +210,19 @@ DG_API dg_status dg_set_target(dg_solver* s, double T_end, long long max_steps);
  * same solver stepped alone. Supported: Euler, FP32 form, 1D or 2D Q^k; all on one device.
  * Synchronises; returns DG_ERR_NONPHYSICAL if any solver failed (check each with dg_sync). */
 DG_API dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps);
+
+/* Batched stepping as dg_batch_run, with the same arguments, classes and results, in one persistent
+ * launch per class instead of a replayed per-step graph: each class's kernel runs all `steps` steps of
+ * its solvers. Its warps take tile items from a queue ordered by (step, stage, solver, item); before
+ * an item a warp waits until every item of that solver's earlier stages has finished (a per-solver
+ * counter on the device), and the last item of a solver's step advances its t and step count and
+ * sets its next dt. Solvers therefore move through their stages independently: a small solver does
+ * not wait for a large one. The launches are cooperative (all blocks resident). Every wait polls a
+ * bounded number of times (about a second); if one gives up, all warps leave and the call returns
+ * DG_ERR_TIMEOUT with the solvers' states undefined (a wait that is not broken lasts at most one
+ * stage of its solver). Allocates a small device scratch block (16 bytes per solver) per call.
+ * Synchronises; DG_ERR_NONPHYSICAL as dg_batch_run. Not while a stream is captured. */
+DG_API dg_status dg_batch_run_persistent(dg_solver* const* solvers, int n, long long steps);
 
 /* Wait for the solver's stream; report the time, the completed step count and any error. */
 DG_API dg_status dg_sync(dg_solver* s, double* t, long long* steps);

@@ -26,6 +26,12 @@ DG_API int dg_probe_fma(int kind, int iters, double* tflops);
  * evaluation of the same transform. */
 DG_API int dg_probe_transform(int variant, long long ncell, int reps, double* ms_per_launch, double* rel_l1);
 
+/* The bounded wait of dg_batch_run_persistent's kernels, on a counter that nothing releases: one warp
+ * polls it poll_limit (at most 2^24) times, 256 ns apart, and gives up. *status: the status word the kernel left
+ * (1 = the wait gave up, as it must); *ms: the launch's duration. Shows that a wait which can never be
+ * satisfied ends, reports, and leaves the context usable. */
+DG_API int dg_probe_wait_timeout(unsigned poll_limit, unsigned* status, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ EXPORTED = ["dg_status_string", "dg_last_error", "dg_params_default", "dg_worksp
             "dg_set_initial", "dg_state_size", "dg_write_state", "dg_write_state_device", "dg_read_state",
             "dg_read_state_device", "dg_step", "dg_advance_to", "dg_advance_steps", "dg_sync", "dg_mass",
             "dg_dims", "dg_kernel_launches", "dg_destroy", "dg_step_noalloc", "dg_set_target",
-            "dg_batch_run", "dg_probe_fma", "dg_probe_transform"]
+            "dg_batch_run", "dg_batch_run_persistent", "dg_probe_fma", "dg_probe_transform",
+            "dg_probe_wait_timeout"]
 
 
 class Mesh(C.Structure):
@@ -90,8 +91,10 @@ def load():
         "dg_step_noalloc": (I, [P(Mesh), I, I, P(Params), V, V, dp, V]),
         "dg_set_target": (I, [V, D, LL]),
         "dg_batch_run": (I, [P(V), I, LL]),
+        "dg_batch_run_persistent": (I, [P(V), I, LL]),
         "dg_probe_fma": (I, [I, I, dp]),
         "dg_probe_transform": (I, [I, LL, I, dp, dp]),
+        "dg_probe_wait_timeout": (I, [C.c_uint, P(C.c_uint), dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -113,10 +116,12 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def batch_run(solvers, steps: int) -> int:
-    """dg_batch_run over a list of Solver objects; returns the status (0 = all ok)."""
+def batch_run(solvers, steps: int, persistent: bool = False) -> int:
+    """dg_batch_run (or dg_batch_run_persistent) over a list of Solver objects; returns the status
+    (0 = all ok)."""
     arr = (C.c_void_p * len(solvers))(*[s.handle.value for s in solvers])
-    return load().dg_batch_run(arr, len(solvers), steps)
+    f = load().dg_batch_run_persistent if persistent else load().dg_batch_run
+    return f(arr, len(solvers), steps)
 
 
 class Solver:

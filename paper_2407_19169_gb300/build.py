@@ -14,12 +14,14 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjf.so")
 # (source, object, defines): stage2d_units.cu is compiled once per (form, degree) of the 2D stage
-# kernel and once for its dispatch tables, so that its slow instantiations compile in parallel.
+# kernel and once for its dispatch tables, dg_batch.cu once for its host code and 1D kernels and once
+# per degree of its 2D kernels, so that the slow instantiations compile in parallel.
 UNITS = [(u, u.replace(".cu", ".o"), []) for u in
          ["dg_api.cu", "aux.cu", "stage1d.cu", "dg_noalloc.cu", "dg_batch.cu", "probes.cu"]] + \
         [("stage2d_units.cu", "stage2d_f%d_k%d.o" % (f, k), ["-DS2_FORM=%d" % f, "-DS2_K=%d" % k])
          for f in range(5) for k in (1, 2, 3)] + \
-        [("stage2d_units.cu", "stage2d_dispatch.o", ["-DS2_DISPATCH"])]
+        [("stage2d_units.cu", "stage2d_dispatch.o", ["-DS2_DISPATCH"])] + \
+        [("dg_batch.cu", "dg_batch_k%d.o" % k, ["-DDG_BATCH_K=%d" % k]) for k in (1, 2, 3)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div=false / -prec-sqrt=false: single-precision division and square root by the hardware
 # approximations (a couple of ulp). They act only on FP32 arithmetic (the FP32 form's stage math);
@@ -59,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             jobs.append((o, cmd))
     if jobs:
         # the slowest units first, so that they start before the pool fills
-        jobs.sort(key=lambda j: ("_k3" not in j[0], "_f0" not in j[0] and "_f3" not in j[0]))
+        jobs.sort(key=lambda j: ("k3" not in j[0], "_f0" not in j[0] and "_f3" not in j[0]))
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
             futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): u for u, cmd in jobs}
             for f in cf.as_completed(futs):

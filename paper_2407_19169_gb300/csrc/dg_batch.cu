@@ -18,6 +18,7 @@
 
 #include <vector>
 
+#include "../../include/dg_probes.h"
 #include "solver.h"
 #include "stage1d.cuh"
 
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(256) batch1d_kernel(const BatchArgs b) {
   if (cur >= 0) item_end(b.inst[cur], b.stage, cur_step, racc, okacc);
 }
 
+#ifndef DG_BATCH_K
 // Per-instance dt at the start of a step (the same rule as the single-solve stage 0).
 __global__ void batch_begin_kernel(const BatchInst* inst, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,6 +245,236 @@ __global__ void batch_end_kernel(const BatchInst* inst, int n) {
   sc->done = (tn >= sc->T_end || st >= sc->max_step) ? 1u : 0u;
 }
 
+
+#endif  // !DG_BATCH_K
+// ---- persistent batched stepping (dg_batch_run_persistent) ----
+// One launch per class runs every step of its instances. The class's work is a queue of items in the
+// order (step, stage, instance, item); a warp takes the next queue index with one atomic, waits until
+// every item of the instance's earlier stages has finished (a per-instance release counter), runs the
+// item and arrives. The last item of an instance's stage releases the next stage; the last of its
+// final stage also advances the instance's step (t, step, done) and sets the next step's dt, the work
+// of the graph path's end and begin kernels. A wait only ever depends on queue indices taken before
+// its own, by warps that are running, so the queue order itself rules out a deadlock; the launch is
+// cooperative all the same, and every wait gives up after a bounded number of polls, sets a status
+// bit and makes all warps leave.
+
+// Per-instance barrier state (zeroed before the launch).
+struct PersistCtl {
+  unsigned long long arrived;   // items of this run finished
+  unsigned int released;        // stages (phases) of this run whose items have all finished
+  unsigned int pad;
+};
+
+enum : unsigned { PERSIST_TIMEOUT = 1u };
+
+struct PersistArgs {
+  const BatchInst* inst;        // the class's instances, item0 ascending
+  PersistCtl* ctl;              // one per instance
+  int ninst;
+  long long nitems;             // items of one phase (one stage of every instance)
+  long long total;              // nitems * 3 * steps
+  long long steps;
+  unsigned long long* queue;    // next queue index (zeroed)
+  unsigned int* status;         // PERSIST_TIMEOUT when a wait gave up
+  unsigned int poll_limit;      // polls of a wait before it gives up
+};
+
+// Wait until `phase` stages of the instance have finished. False if the wait gave up (or another
+// warp's did): the caller leaves.
+__device__ __forceinline__ bool persist_wait(const PersistCtl* C, long long phase, unsigned* status,
+                                             unsigned poll_limit) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0 && phase > 0) {
+    unsigned polls = 0;
+    while (*(const volatile unsigned*)&C->released < (unsigned)phase) {
+      if (*(volatile unsigned*)status) {
+        ok = 0;
+        break;
+      }
+      if (++polls > poll_limit) {
+        atomicOr(status, PERSIST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(256);
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __threadfence();   // the released stage's stores before this item's loads
+  return ok != 0;
+}
+
+// End of the step of one instance (the graph path's end kernel) and, if another step follows in this
+// run, the start of the next (its begin kernel).
+__device__ __forceinline__ void persist_step_advance(const BatchInst& I, bool next) {
+  volatile DevScalars* sc = I.sc;
+  if (sc->done | sc->err) return;
+  const double tn = sc->is_last ? sc->T_end : sc->t + sc->dt;
+  const long long st = sc->step + 1;
+  sc->t = tn;
+  sc->step = st;
+  const bool done = (tn >= sc->T_end || st >= sc->max_step);
+  sc->done = done ? 1u : 0u;
+  if (done || !next) return;
+  const double rate = __longlong_as_double((long long)sc->rate_bits[st & 1]);
+  if (!(rate > 0.0) || !isfinite(rate)) {
+    atomicOr(&I.sc->err, ERRB_RATE);
+    return;
+  }
+  const double T = sc->T_end, dtc = I.cfl / rate;
+  const bool last = (tn + dtc >= T);
+  sc->dt = last ? T - tn : dtc;
+  sc->is_last = last ? 1u : 0u;
+  sc->rate_bits[(st + 1) & 1] = 0ull;
+}
+
+// Arrival of one finished (or skipped) item; the last item of an instance's stage releases it.
+__device__ __forceinline__ void persist_arrive(const PersistArgs& P, const BatchInst& I, PersistCtl* C,
+                                               long long phase) {
+  __threadfence();   // this lane's stores before the arrival
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence();
+    const unsigned long long items = (unsigned long long)I.nstrips * (unsigned long long)I.nchunks;
+    const unsigned long long prev = atomicAdd(&C->arrived, 1ull);
+    if (prev + 1 == (unsigned long long)(phase + 1) * items) {
+      if (phase % 3 == 2) persist_step_advance(I, phase / 3 + 1 < P.steps);
+      __threadfence();
+      atomicExch(&C->released, (unsigned)(phase + 1));
+    }
+  }
+  __syncwarp();
+}
+
+// The queue index a warp takes next (P.total when the queue is empty or a wait gave up).
+__device__ __forceinline__ long long persist_take(const PersistArgs& P) {
+  long long k = 0;
+  if ((threadIdx.x & 31) == 0)
+    k = *(volatile unsigned*)P.status ? P.total : (long long)atomicAdd(P.queue, 1ull);
+  return __shfl_sync(0xffffffffu, k, 0);
+}
+
+template <int K, bool LIM>
+__global__ void __launch_bounds__(256) persist2d_kernel(const PersistArgs P) {
+  using S = Stage2D<K, EQ_EULER, BASIS_Q, PrecF32M, false, LIM, true>;
+  using T = float;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* ws = (T*)(dyn_smem + S::warp_bytes() * (threadIdx.x >> 5));
+  for (;;) {
+    const long long k = persist_take(P);
+    if (k >= P.total) break;
+    const long long phase = k / P.nitems, w = k - phase * P.nitems;
+    const int ii = find_inst(P.inst, P.ninst, w);
+    const BatchInst& I = P.inst[ii];
+    PersistCtl* C = P.ctl + ii;
+    if (!persist_wait(C, phase, P.status, P.poll_limit)) break;
+    const int stage = (int)(phase % 3);
+    volatile DevScalars* vs = I.sc;
+    if (!(vs->done | vs->err)) {
+      const long long step = vs->step;
+      const double dt = vs->dt;
+      const int p = (int)(step & 1);
+      Stage2DArgs a;
+      a.uin = stage == 0 ? I.buf[p] : (stage == 1 ? I.buf[1 - p] : I.buf[2]);
+      a.un = I.buf[p];
+      a.uout = stage == 1 ? I.buf[2] : I.buf[1 - p];
+      a.nx = I.nx;
+      a.ny = I.ny;
+      a.ncell = I.ncell;
+      a.hx = I.hx;
+      a.hy = I.hy;
+      a.bcx = I.bcx;
+      a.bcy = I.bcy;
+      a.c0 = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+      a.c1 = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+      a.stage = stage;
+      a.filter_on = I.filter_on;
+      a.gamma = I.gamma;
+      a.ax = I.ax;
+      a.ay = I.ay;
+      a.cfl = I.cfl;
+      a.H = I.H;
+      a.nstrips = I.nstrips;
+      a.nchunks = I.nchunks;
+      a.positivity = I.positivity;
+      a.hybrid = 0;
+      a.hyb = HybridOut{};
+      a.sc = I.sc;
+      a.cf = I.cf;
+      a.cd = I.cd;
+      const long long local = w - I.item0;
+      double r = 0.0;
+      T rt = T(0);
+      bool ok = true;
+      S::item(a, dt, (int)(local % I.nstrips), (int)(local / I.nstrips), ws, r, rt, ok);
+      item_end(I, stage, step, (double)rt, ok);
+    }
+    persist_arrive(P, I, C, phase);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) persist1d_kernel(const PersistArgs P) {
+  using S = Stage1D<K, EQ_EULER, PrecF32M, false, true>;
+  using T = float;
+  for (;;) {
+    const long long k = persist_take(P);
+    if (k >= P.total) break;
+    const long long phase = k / P.nitems, w = k - phase * P.nitems;
+    const int ii = find_inst(P.inst, P.ninst, w);
+    const BatchInst& I = P.inst[ii];
+    PersistCtl* C = P.ctl + ii;
+    if (!persist_wait(C, phase, P.status, P.poll_limit)) break;
+    const int stage = (int)(phase % 3);
+    volatile DevScalars* vs = I.sc;
+    if (!(vs->done | vs->err)) {
+      const long long step = vs->step;
+      const double dt = vs->dt;
+      const int p = (int)(step & 1);
+      Stage1DArgs a;
+      a.uin = stage == 0 ? I.buf[p] : (stage == 1 ? I.buf[1 - p] : I.buf[2]);
+      a.un = I.buf[p];
+      a.uout = stage == 1 ? I.buf[2] : I.buf[1 - p];
+      a.nx = I.nx;
+      a.ncell = I.ncell;
+      a.h = I.hx;
+      a.bc = I.bcx;
+      a.c0 = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+      a.c1 = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+      a.stage = stage;
+      a.filter_on = I.filter_on;
+      a.gamma = I.gamma;
+      a.ax = I.ax;
+      a.cfl = I.cfl;
+      a.nwarps = I.nstrips;
+      a.positivity = I.positivity;
+      a.hybrid = 0;
+      a.hyb = HybridOut{};
+      a.sc = I.sc;
+      a.inv_h_d = I.inv_h_d;
+      a.scl_d = I.scl_d;
+      a.inv_h_f = I.inv_h_f;
+      a.scl_f = I.scl_f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        a.wpow_d[m] = I.wpow_d[m];
+        a.wpow_f[m] = I.wpow_f[m];
+      }
+      {
+        const double c0 = a.c0;
+        a.c0_hi = (float)c0;
+        a.c0_lo = (float)(c0 - (double)a.c0_hi);
+      }
+      double r = 0.0;
+      T rt = T(0);
+      bool ok = true;
+      S::item(a, dt, w - I.item0, r, rt, ok);
+      item_end(I, stage, step, (double)rt, ok);
+    }
+    persist_arrive(P, I, C, phase);
+  }
+}
+
 struct BatchLauncher {
   cudaError_t (*launch)(const BatchArgs&, unsigned grid, unsigned block, size_t smem, cudaStream_t s);
   cudaError_t (*set_smem)(size_t bytes);
@@ -250,6 +482,33 @@ struct BatchLauncher {
   int (*blocks_per_sm)(unsigned block, size_t smem);  // 2D: resident blocks per SM
 };
 
+// The persistent kernel of a class and the row-slot bytes per warp it needs (2D; 1D: 0).
+struct PersistLauncher {
+  const void* fn;
+  size_t warp_bytes;
+};
+// The 2D kernels of degree K (graph path and persistent path, without / with the limiter code) are
+// compiled in units of their own (this file with -DDG_BATCH_K=K), in parallel; the main unit reaches
+// them through these specialisations.
+template <int K, bool LIM>
+BatchLauncher make_b2();
+template <int K, bool LIM>
+PersistLauncher make_p2();
+#define DG_BATCH_DECLARE(K)          \
+  template <>                        \
+  BatchLauncher make_b2<K, false>(); \
+  template <>                        \
+  BatchLauncher make_b2<K, true>();  \
+  template <>                        \
+  PersistLauncher make_p2<K, false>(); \
+  template <>                        \
+  PersistLauncher make_p2<K, true>();
+DG_BATCH_DECLARE(1)
+DG_BATCH_DECLARE(2)
+DG_BATCH_DECLARE(3)
+#undef DG_BATCH_DECLARE
+
+#ifdef DG_BATCH_K
 template <int K, bool LIM>
 static cudaError_t launch_b2(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
   batch2d_kernel<K, EQ_EULER, BASIS_Q, PrecF32M, LIM><<<g, bl, sm, s>>>(b);
@@ -269,10 +528,31 @@ static int occ_b2(unsigned block, size_t smem) {
   return n;
 }
 template <int K, bool LIM>
-static BatchLauncher make_b2() {
+static BatchLauncher make_b2_impl() {
   return {&launch_b2<K, LIM>, &smem_b2<K, LIM>, Stage2D<K, EQ_EULER, BASIS_Q, PrecF32M, false, LIM>::warp_bytes(),
           &occ_b2<K, LIM>};
 }
+template <int K, bool LIM>
+static PersistLauncher make_p2_impl() {
+  return {(const void*)&persist2d_kernel<K, LIM>, Stage2D<K, EQ_EULER, BASIS_Q, PrecF32M, false, LIM, true>::warp_bytes()};
+}
+template <>
+BatchLauncher make_b2<DG_BATCH_K, false>() {
+  return make_b2_impl<DG_BATCH_K, false>();
+}
+template <>
+BatchLauncher make_b2<DG_BATCH_K, true>() {
+  return make_b2_impl<DG_BATCH_K, true>();
+}
+template <>
+PersistLauncher make_p2<DG_BATCH_K, false>() {
+  return make_p2_impl<DG_BATCH_K, false>();
+}
+template <>
+PersistLauncher make_p2<DG_BATCH_K, true>() {
+  return make_p2_impl<DG_BATCH_K, true>();
+}
+#else  // the main unit: 1D kernels and the selection tables
 template <int K>
 static cudaError_t launch_b1(const BatchArgs& b, unsigned g, unsigned bl, size_t sm, cudaStream_t s) {
   batch1d_kernel<K, EQ_EULER, PrecF32M><<<g, bl, sm, s>>>(b);
@@ -298,11 +578,35 @@ static BatchLauncher batch_launcher(int dim, int K, bool lim) {
   return {nullptr, nullptr, 0, nullptr};
 }
 
+static PersistLauncher persist_launcher(int dim, int K, bool lim) {
+  if (dim == 2) {
+    switch (K) {
+      case 1: return lim ? make_p2<1, true>() : make_p2<1, false>();
+      case 2: return lim ? make_p2<2, true>() : make_p2<2, false>();
+      case 3: return lim ? make_p2<3, true>() : make_p2<3, false>();
+    }
+  } else {
+    switch (K) {
+      case 1: return {(const void*)&persist1d_kernel<1>, 0};
+      case 2: return {(const void*)&persist1d_kernel<2>, 0};
+      case 3: return {(const void*)&persist1d_kernel<3>, 0};
+    }
+  }
+  return {nullptr, 0};
+}
+
+// Polls of a persistent-kernel wait before it gives up (about a second at 256 ns a poll; a wait
+// that is not broken lasts at most one stage of its instance, milliseconds)
+constexpr unsigned PERSIST_POLL_LIMIT = 1u << 22;
+
+#endif  // DG_BATCH_K
+
 }  // namespace dgk
 
+#ifndef DG_BATCH_K
 using namespace dgk;
 
-extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps) {
+static dg_status batch_run(dg_solver* const* solvers, int n, long long steps, bool persistent) {
   if (!solvers || n < 1 || steps < 0) return DG_ERR_ARG;
   int dev0 = -1;
   for (int i = 0; i < n; ++i) {
@@ -431,8 +735,10 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
     }
     if (cls_count[c] > 0 && BL[c].set_smem) e = BL[c].set_smem(BL[c].warp_bytes * cls_wpb[c]);
   }
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
+  unsigned char* pscr = nullptr;
+  bool timed_out = false;
+  if (!persistent && e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+  if (!persistent && e == cudaSuccess) {
     cudaError_t ce = cudaSuccess;
     const unsigned nb = (unsigned)((host.size() + 127) / 128);
     batch_begin_kernel<<<nb, 128, 0, main>>>(dinst, (int)host.size());
@@ -469,10 +775,68 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
     e = cudaStreamEndCapture(main, &graph);
     if (ce != cudaSuccess) e = ce;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  for (long long i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, main);
+  if (!persistent) {
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    for (long long i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, main);
+  } else if (e == cudaSuccess) {
+    // persistent path: the begin kernel sets the first step's dt, then one cooperative launch per
+    // class (classes in parallel) runs all the steps; scratch: the instances' barrier states, the
+    // classes' queue counters and the status word
+    const size_t ctl_bytes = sizeof(PersistCtl) * host.size();
+    const size_t scr = ctl_bytes + sizeof(unsigned long long) * NCLS + 16;
+    e = cudaMalloc(&pscr, scr);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pscr, 0, scr, main);
+    PersistCtl* dctl = (PersistCtl*)pscr;
+    unsigned long long* dq = (unsigned long long*)(pscr + ctl_bytes);
+    unsigned* dstatus = (unsigned*)(dq + NCLS);
+    if (e == cudaSuccess) {
+      batch_begin_kernel<<<(unsigned)((host.size() + 127) / 128), 128, 0, main>>>(dinst, (int)host.size());
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(fork, main);
+    for (int c = 0; c < NCLS && e == cudaSuccess; ++c) {
+      if (cls_count[c] == 0) continue;
+      const PersistLauncher PL = persist_launcher(c < 3 ? 1 : 2, c % 3 + 1, c >= 6);
+      const int wpb = c < 3 ? 4 : cls_wpb[c];
+      const unsigned block = 32u * wpb;
+      const size_t smem = PL.warp_bytes * wpb;
+      e = cudaFuncSetAttribute(PL.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int bps = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, PL.fn, (int)block, smem);
+      if (e != cudaSuccess) break;
+      if (bps < 1) {
+        e = cudaErrorInvalidConfiguration;
+        break;
+      }
+      // all blocks resident (cooperative launch); no more warps than one stage of the class has items
+      long long grid = (long long)bps * nsm;
+      const long long need = (cls_items[c] + wpb - 1) / wpb;
+      if (grid > need) grid = need;
+      PersistArgs P;
+      P.inst = dinst + cls_begin[c];
+      P.ctl = dctl + cls_begin[c];
+      P.ninst = cls_count[c];
+      P.nitems = cls_items[c];
+      P.total = cls_items[c] * 3 * steps;
+      P.steps = steps;
+      P.queue = dq + c;
+      P.status = dstatus;
+      P.poll_limit = PERSIST_POLL_LIMIT;
+      void* args[] = {&P};
+      e = cudaStreamWaitEvent(side[c], fork, 0);
+      if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(PL.fn, dim3((unsigned)grid), dim3(block), args, smem, side[c]);
+      if (e == cudaSuccess) e = cudaEventRecord(join[c], side[c]);
+    }
+    for (int c = 0; c < NCLS && e == cudaSuccess; ++c)
+      if (cls_count[c] > 0) e = cudaStreamWaitEvent(main, join[c], 0);
+    unsigned hstatus = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);
+    timed_out = e == cudaSuccess && (hstatus & PERSIST_TIMEOUT) != 0;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(main);
   if (e != cudaSuccess) status = DG_ERR_CUDA;
+  else if (timed_out) status = DG_ERR_TIMEOUT;
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   for (int c = 0; c < NCLS; ++c) {
@@ -481,10 +845,12 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
   }
   if (fork) cudaEventDestroy(fork);
   if (dinst) cudaFree(dinst);
+  if (pscr) cudaFree(pscr);
   if (status != DG_OK) return status;
   int present = 0;
   for (int c = 0; c < NCLS; ++c) present += cls_count[c] > 0;
-  solvers[0]->launches += steps * (2 + 3LL * present);    // the graph's kernel nodes, once per step
+  // the graph's kernel nodes once per step; the persistent path's begin kernel and class launches
+  solvers[0]->launches += persistent ? 1 + present : steps * (2 + 3LL * present);
   for (int i = 0; i < n; ++i) {
     dg_solver* s = solvers[i];
     if (solver_pull_control(s) != DG_OK) return DG_ERR_CUDA;
@@ -492,3 +858,45 @@ extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long st
   }
   return status;
 }
+
+extern "C" dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps) {
+  return batch_run(solvers, n, steps, false);
+}
+
+extern "C" dg_status dg_batch_run_persistent(dg_solver* const* solvers, int n, long long steps) {
+  return batch_run(solvers, n, steps, true);
+}
+
+// One warp waits on a barrier state that nothing releases (phase 1 of an instance with no items).
+__global__ void wait_timeout_probe_kernel(PersistCtl* ctl, unsigned* status, unsigned poll_limit) {
+  persist_wait(ctl, 1, status, poll_limit);
+}
+
+extern "C" int dg_probe_wait_timeout(unsigned poll_limit, unsigned* status, double* ms) {
+  if (!status || !ms || poll_limit > (1u << 24)) return -1;
+  unsigned char* d = nullptr;
+  if (cudaMalloc(&d, 64) != cudaSuccess) return -2;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, 64, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>((PersistCtl*)d, (unsigned*)(d + 32), poll_limit);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status, d + 32, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float f = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+  *ms = f;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(d);
+  return e == cudaSuccess ? 0 : -6;
+}
+#endif  // !DG_BATCH_K

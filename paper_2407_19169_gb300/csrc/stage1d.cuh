@@ -66,14 +66,15 @@ inline void stage1d_consts(Stage1DArgs& a) {
 
 // OE = true: the OEDG form of the damping (the kernel stores u~ unfiltered with the jump sums A_v(l)
 // and the reductions of OedgOut; the OEDG filter kernel applies the damping).
-template <int K, int EQ, class PR, bool OE = false>
+// COH = true: state loads through L2 (Store), for the persistent batched kernel.
+template <int K, int EQ, class PR, bool OE = false, bool COH = false>
 struct Stage1D {
   using T = typename PR::T;
   static constexpr int NM = K + 1;
   static constexpr int NV = NVars<EQ, 1>::value;
   static constexpr int NQ = K + 1;
   using GR = GaussRule<NQ>;
-  using ST = Store<PR, NV, NM>;
+  using ST = Store<PR, NV, NM, COH>;
   // FP32 form, Euler (three variables): the double-float cell averages of variables 0 and 1 in one
   // register pair (packed FP32 instructions, bitwise the same results). Degrees 1 and 2 only
   // (4 M cells: k = 1 0.108 -> 0.105 ms per launch, k = 2 -1 %; k = 3 +0.4 %).

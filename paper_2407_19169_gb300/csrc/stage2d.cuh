@@ -123,9 +123,16 @@ struct PrecF32M {
   static constexpr bool MIXED = true;
 };
 
-template <class PR, int NV, int NM>
+// COH = true: coherent loads through L2 (ld.global.cg) instead of the read-only path, for kernels that
+// read states written earlier by other blocks of the same launch (the persistent batched kernel).
+template <class PR, int NV, int NM, bool COH = false>
 struct Store {
   using T = typename PR::T;
+  template <class V>
+  static __device__ __forceinline__ V ld(const V* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+  }
   // the FP32 form with an even number of variables keeps them in pairs (F32Layout)
   static constexpr bool PAIRED = PR::MIXED && (NV % 2) == 0;
   // load u[v][m] (and the low word of the mode-0 double-float in lo0[v]).
@@ -136,7 +143,7 @@ struct Store {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
 #pragma unroll
-        for (int m = 0; m < NM; ++m) u[v][m] = __ldg(b + (long long)(v * NM + m) * ncell + c);
+        for (int m = 0; m < NM; ++m) u[v][m] = ld(b + (long long)(v * NM + m) * ncell + c);
         lo0[v] = T(0);
       }
     } else if constexpr (PAIRED) {
@@ -144,21 +151,21 @@ struct Store {
 #pragma unroll
       for (int pr = 0; pr < NV / 2; ++pr) {
         const float* r = (const float*)base + pr * L.region_words();
-        const float4 a = __ldg((const float4*)r + c);
+        const float4 a = ld((const float4*)r + c);
         u[2 * pr][0] = a.x;
         u[2 * pr + 1][0] = a.y;
         lo0[2 * pr] = a.z;
         lo0[2 * pr + 1] = a.w;
 #pragma unroll
         for (int q = 0; q < (NM - 1) / 2; ++q) {
-          const float4 x = __ldg((const float4*)r + ncell * (1 + q) + c);
+          const float4 x = ld((const float4*)r + ncell * (1 + q) + c);
           u[2 * pr][1 + 2 * q] = x.x;
           u[2 * pr + 1][1 + 2 * q] = x.y;
           u[2 * pr][2 + 2 * q] = x.z;
           u[2 * pr + 1][2 + 2 * q] = x.w;
         }
         if constexpr (((NM - 1) & 1) != 0) {
-          const float2 y = __ldg((const float2*)(r + 4 * ncell * (1 + (NM - 1) / 2)) + c);
+          const float2 y = ld((const float2*)(r + 4 * ncell * (1 + (NM - 1) / 2)) + c);
           u[2 * pr][NM - 1] = y.x;
           u[2 * pr + 1][NM - 1] = y.y;
         }
@@ -168,11 +175,11 @@ struct Store {
       const float* bh = (const float*)((const char*)base + sizeof(float2) * (size_t)NV * ncell);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        float2 a = __ldg(b0 + (long long)v * ncell + c);
+        float2 a = ld(b0 + (long long)v * ncell + c);
         u[v][0] = a.x;
         lo0[v] = a.y;
 #pragma unroll
-        for (int m = 1; m < NM; ++m) u[v][m] = __ldg(bh + (long long)(v * (NM - 1) + m - 1) * ncell + c);
+        for (int m = 1; m < NM; ++m) u[v][m] = ld(bh + (long long)(v * (NM - 1) + m - 1) * ncell + c);
       }
     }
   }
@@ -230,7 +237,8 @@ struct Store {
 // jump sums A_v(l) and the reductions of OedgOut, and the OEDG filter kernel applies the damping.
 // LIM = false: no positivity or hybrid limiter code (a.positivity and a.hybrid are ignored); a
 // smaller loop body for the solves that use neither (2048^2 Q2, FP32 form: 0.748 -> 0.702 ms).
-template <int K, int EQ, int BASIS, class PR, bool OE = false, bool LIM = true>
+// COH = true: state loads through L2 (Store), for the persistent batched kernel.
+template <int K, int EQ, int BASIS, class PR, bool OE = false, bool LIM = true, bool COH = false>
 struct Stage2D {
   using T = typename PR::T;
   using MB = Modes<K, BASIS>;
@@ -251,7 +259,7 @@ struct Stage2D {
   static constexpr bool PACK_TRACES = PACK && K <= 2;
   static constexpr bool PACK_DF = PACK && K >= 2;
   using GR = GaussRule<NQ>;
-  using ST = Store<PR, NV, NM>;
+  using ST = Store<PR, NV, NM, COH>;
   using TB = Tab2D<K, BASIS>;
 
   // Row slots of u~ (rows t, t-1, t-2). Packed FP32 form: per lane, one contiguous block per (slot,

@@ -13,14 +13,17 @@ F32 = N.PREC_FP32_MIXED
 
 def make(spec):
     kind, n, k = spec["kind"], spec["n"], spec["k"]
+    pos = spec.get("pos", 0)
     if kind == "riemann1d":
-        s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4, precision=F32)
+        s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4, precision=F32,
+                     positivity=pos)
         s.set_initial(N.IC_RIEMANN1D, I.riemann1d_params(spec["seed"]))
     elif kind == "entropy1d":
         s = N.Solver(dim=1, nx=n, k=k, eq=N.EQ_EULER, bc=(N.BC_PERIODIC,) * 4, precision=F32)
         s.set_initial(N.IC_ENTROPY1D, [1.0, 0.2, 2 * np.pi, 1.0, 1.0])
     elif kind == "quadrant2d":
-        s = N.Solver(dim=2, nx=n, ny=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4, precision=F32)
+        s = N.Solver(dim=2, nx=n, ny=n, k=k, eq=N.EQ_EULER, bc=(N.BC_OUTFLOW,) * 4, precision=F32,
+                     positivity=pos)
         s.set_initial(N.IC_QUADRANT2D, I.quadrant_params(spec["seed"]))
     else:
         s = N.Solver(dim=2, nx=n, ny=n, x0=0, x1=10, y0=-5, y1=5, k=k, eq=N.EQ_EULER,
