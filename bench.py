@@ -58,8 +58,8 @@ def peaks():
 # Sources whose compiled form is the timed stage kernel: the DRAM traffic recorded in profiles/ is
 # reported only while they are unchanged since the capture.
 KERNEL_SOURCES = ["paper_2407_19169_gb300/csrc/stage2d.cuh", "paper_2407_19169_gb300/csrc/dg_device.cuh",
-                  "paper_2407_19169_gb300/csrc/stage_common.cuh", "paper_2407_19169_gb300/csrc/stage2d_f32.cu",
-                  "paper_2407_19169_gb300/build.py"]
+                  "paper_2407_19169_gb300/csrc/stage_common.cuh", "paper_2407_19169_gb300/csrc/stage2d_units.cu",
+                  "paper_2407_19169_gb300/csrc/dg_tables.cuh"]
 TRAFFIC_PROFILE = "profiles/stage2d_f32_q2_euler_2048_traffic.md"
 
 
