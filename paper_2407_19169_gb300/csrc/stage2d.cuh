@@ -423,7 +423,9 @@ struct Stage2D {
 
   // M[l] = sum_g w_g phi_l(x_g) F[g], l = 0..K, phi_l = P_l (DERIV = 0) or P_l' (DERIV = 1), from the
   // node-pair sums F[g] + F[NQ-1-g] (phi_l even) and differences (phi_l odd). M[0] = 0 for DERIV = 1.
-  template <int DERIV, class VT>
+  // HALF: the moments of F / 2 (the weights halved, which is exact), for the LLF fluxes formed as
+  // twice their value.
+  template <int DERIV, class VT, bool HALF = false>
   static __device__ __forceinline__ void gauss_moments(const VT (&F)[NQ], VT (&M)[K + 1]) {
     using S = typename vtraits<VT>::S;
     VT s[NQ / 2], d[NQ / 2];
@@ -438,34 +440,36 @@ struct Stage2D {
       VT acc = vtraits<VT>::zero();
       sfor<NQ / 2>([&](auto G) {
         constexpr int g = decltype(G)::value;
-        constexpr double w = DERIV ? TB::WD[l * NQ + g] : TB::WP[l * NQ + g];
+        constexpr double w = (DERIV ? TB::WD[l * NQ + g] : TB::WP[l * NQ + g]) * (HALF ? 0.5 : 1.0);
         if constexpr (w != 0.0) {
           if constexpr (even) acc = vmad(s[g], (S)w, acc);
           else acc = vmad(d[g], (S)w, acc);
         }
       });
       if constexpr ((NQ & 1) != 0 && even) {
-        constexpr double w = DERIV ? TB::WD[l * NQ + NQ / 2] : TB::WP[l * NQ + NQ / 2];
+        constexpr double w = (DERIV ? TB::WD[l * NQ + NQ / 2] : TB::WP[l * NQ + NQ / 2]) * (HALF ? 0.5 : 1.0);
         if constexpr (w != 0.0) acc = vmad(F[NQ / 2], (S)w, acc);
       }
       M[l] = acc;
     });
   }
 
-  // LLF flux at one face point, 1/2 (f(uL) + f(uR)) - 1/2 alpha (uR - uL), alpha the larger spectral
-  // radius, with the combination on pairs of variables (packed form): fh[vp] = {fh_2vp, fh_2vp+1}.
+  // Twice the LLF flux at one face point, f(uL) + f(uR) - alpha (uR - uL), alpha the larger spectral
+  // radius, with the combination on pairs of variables (packed form): fh[vp] = 2 {fh_2vp, fh_2vp+1}.
+  // The halving goes into the moments' weights (gauss_moments<.., true>); scaling by 2 commutes with
+  // rounding, so the moments are bitwise those of the flux itself.
   template <int DIR>
   static __device__ __forceinline__ void llf_pairs(const T (&uL)[NV], const T (&uR)[NV], f2 (&fh)[NV / 2], T gam,
                                                    T gm1, T ax, T ay) {
     T fL[NV], fR[NV];
     flux2d<EQ, DIR>(uL, fL, gm1, ax, ay);
     flux2d<EQ, DIR>(uR, fR, gm1, ax, ay);
-    const T ha = T(-0.5) * nan_max(speed2d<EQ, DIR>(uL, gam, gm1, ax, ay), speed2d<EQ, DIR>(uR, gam, gm1, ax, ay));
+    const T na = -nan_max(speed2d<EQ, DIR>(uL, gam, gm1, ax, ay), speed2d<EQ, DIR>(uR, gam, gm1, ax, ay));
 #pragma unroll
     for (int vp = 0; vp < NV / 2; ++vp) {
       const f2 sum = f2{fL[2 * vp], fL[2 * vp + 1]} + f2{fR[2 * vp], fR[2 * vp + 1]};
       const f2 dif = f2{uR[2 * vp], uR[2 * vp + 1]} - f2{uL[2 * vp], uL[2 * vp + 1]};
-      fh[vp] = vfma(dif, f2{ha, ha}, vscale(sum, T(0.5)));
+      fh[vp] = vfma(dif, f2{na, na}, sum);
     }
   }
 
@@ -958,6 +962,8 @@ struct Stage2D {
       T bx2 = T(0), by2 = T(0), invH2 = T(0);
       bool phys2 = true;
 
+      // row slots of rows t, t-1, t-2, rotated once per row (row r in slot r mod 3)
+      int sl0 = slot_of(yb - 2), sl1 = slot_of(yb - 3), sl2 = slot_of(yb - 4);
 #pragma unroll 1
       for (int t = yb - 2; t <= ye + 1; ++t) {
         const bool grow = !pery && (t < 0 || t >= ny);
@@ -995,7 +1001,7 @@ struct Stage2D {
                 f2 F[NQ], M[K + 1];
 #pragma unroll
                 for (int g = 0; g < NQ; ++g) F[g] = Fh2[g][vp];
-                gauss_moments<0>(F, M);
+                gauss_moments<0, f2, true>(F, M);
 #pragma unroll
                 for (int p = 0; p <= K; ++p) {
                   Mh[2 * vp][p] = M[p].x;
@@ -1016,7 +1022,7 @@ struct Stage2D {
             }
             // finalise u~ of row t-1 with its top-face term (P_q(+1) = 1)
             if (t - 1 >= yb - 1 && t - 1 <= ye) {
-              const int s = slot_of(t - 1);
+              const int s = sl1;
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
                 if constexpr (PR::MIXED && !PACK) {
@@ -1099,8 +1105,8 @@ struct Stage2D {
                   FRv[g] = FR2[g][vp];
                   FLv[g] = FL2[g][vp];
                 }
-                gauss_moments<0>(FRv, MRp);
-                gauss_moments<0>(FLv, MLp);
+                gauss_moments<0, f2, true>(FRv, MRp);
+                gauss_moments<0, f2, true>(FLv, MLp);
 #pragma unroll
                 for (int p = 0; p <= K; ++p) {
                   MR[v0][p] = MRp[p].x;
@@ -1174,7 +1180,7 @@ struct Stage2D {
           }
           volume(u, acc, sx, sy, gm1, ax, ay);
 
-          const int s = slot_of(t);
+          const int s = sl0;
           T un_[NV][NM], unlo[NV];
           if (a.stage > 0) ST::load(a.un, a.ncell, cell, un_, unlo);
           // cell average in double-float from the edge integrals, each formed once per edge:
@@ -1265,12 +1271,12 @@ struct Stage2D {
           for (int v = 0; v < NV; ++v) {
             if constexpr (PACK) {
               if ((v & 1) == 0) {
-                const float4 x = pblock(ws, slot_of(t - 1), v / 2, lane)[0];   // {v, v+1} of mode 0 (and 1)
+                const float4 x = pblock(ws, sl1, v / 2, lane)[0];   // {v, v+1} of mode 0 (and 1)
                 ub[v] = x.x;
                 ub[v + 1] = x.y;
               }
             } else {
-              ub[v] = *slot_ptr(ws, slot_of(t - 1), v, 0, lane);
+              ub[v] = *slot_ptr(ws, sl1, v, 0, lane);
             }
           }
           avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx1, by1, invH1, phys1);
@@ -1283,7 +1289,7 @@ struct Stage2D {
         T eta2 = T(0);                                            // hybrid: eta of row t-2
         if (a.filter_on && (need_v || filt_row)) {
           T eta_v = T(0), eta_h = T(0);
-          const int s1 = slot_of(t - 1), s2 = slot_of(t - 2);
+          const int s1 = sl1, s2 = sl2;
           // groups of variables (pairs in packed FP32, else one variable): the jumps are linear in
           // the modes, each group's chain is the scalar chain of every variable in it
           sfor<NG>([&](auto G_) {
@@ -1347,6 +1353,16 @@ struct Stage2D {
                 }
                 continue;
               }
+              if constexpr (PACK && !OE) {
+                // Q of the pair's two variables in one 64-bit word per lane
+                f2* q2 = (f2*)wq + ((g * LMAX + (l - 1)) << 5) + lane;
+                if (filt_row) {
+                  const f2 x = vfma(shc, f2{by2, by2}, *q2);   // Q of row t-2 + its top face
+                  sig[l] = fmax(fmax(sig[l], x.x), x.y);
+                }
+                if (need_v) *q2 = vfma(shc, f2{by1, by1}, vscale(av, bx1));   // Q of row t-1
+                continue;
+              }
               sfor<GW>([&](auto J_) {
                 constexpr int j = decltype(J_)::value, v = g * GW + j;
                 T* q = wq + ((v * LMAX + (l - 1)) << 5) + lane;
@@ -1368,7 +1384,7 @@ struct Stage2D {
           }
         }
         if (filt_row) {
-          const int s2 = slot_of(t - 2);
+          const int s2 = sl2;
           T uo[NV][NM], lo[NV];
           if constexpr (PACK) {
 #pragma unroll
@@ -1483,6 +1499,10 @@ struct Stage2D {
         by2 = by1;
         invH2 = invH1;
         phys2 = phys1;
+        const int sfree = sl2;
+        sl2 = sl1;
+        sl1 = sl0;
+        sl0 = sfree;
       }
     }
     if ((LIM && a.hybrid)) hybrid_max(a.hyb, my_eta);
