@@ -342,6 +342,14 @@ struct Stage2D {
 
   // row slot of row r (rows >= -2 occur; keep the index in 0..2)
   static __device__ __forceinline__ int slot_of(int r) { return ((r % 3) + 3) % 3; }
+  // r mod n for r in [-2, n + 1] and n >= 1 (the rows and columns a tile touches), without division
+  static __device__ __forceinline__ int wrap_near(int r, int n) {
+    r += r < 0 ? n : 0;
+    r += r < 0 ? n : 0;
+    r -= r >= n ? n : 0;
+    r -= r >= n ? n : 0;
+    return r;
+  }
   static __device__ __forceinline__ T* slot_ptr(T* ws, int s, int v, int m, int lane) {
     if constexpr (PACK) return ws + lane * LS + ((s * (NV / 2) + v / 2) * NMEP + m) * 2 + (v & 1);
     else return ws + (((s * NV + v) * NME + m) << 5) + lane;
@@ -967,14 +975,14 @@ struct Stage2D {
 #pragma unroll 1
       for (int t = yb - 2; t <= ye + 1; ++t) {
         const bool grow = !pery && (t < 0 || t >= ny);
-        const int ty = pery ? ((t % ny) + ny) % ny : (t < 0 ? 0 : (t >= ny ? ny - 1 : t));
+        const int ty = pery ? wrap_near(t, ny) : (t < 0 ? 0 : (t >= ny ? ny - 1 : t));
         const long long cell = (long long)ty * nx + xc;
         T u[NV][NM], lo0[NV];
         ST::load(a.uin, a.ncell, cell, u, lo0);
         if constexpr (ST::PAIRED) {
           // the next row of the stage input, and this row of u^n (read after the volume integral)
           const int tn = t + 1;
-          const int tyn = pery ? ((tn % ny) + ny) % ny : (tn < 0 ? 0 : (tn >= ny ? ny - 1 : tn));
+          const int tyn = pery ? (ty + 1 >= ny ? ty + 1 - ny : ty + 1) : (tn < 0 ? 0 : (tn >= ny ? ny - 1 : tn));
           ST::prefetch(a.uin, a.ncell, (long long)tyn * nx + xc);
           if (a.stage > 0) ST::prefetch(a.un, a.ncell, cell);
         }
@@ -1281,7 +1289,7 @@ struct Stage2D {
           }
           avg_params<EQ, 2>(ub, gam, gm1, ax, ay, bx1, by1, invH1, phys1);
         }
-        const int ty2 = pery ? ((t - 2) % ny + ny) % ny : t - 2;
+        const int ty2 = t - 2;   // used only while row t-2 is filtered, a row of the chunk
         const long long cell2 = (long long)ty2 * nx + xc;       // the cell filtered in this iteration
         T sig[LMAX + 1];
 #pragma unroll
