@@ -1346,13 +1346,16 @@ struct Stage2D {
             VG sv[LMAX + 1], sh[LMAX + 1];
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) sv[l] = sh[l] = z;
-            if (need_v) vertical_jumps(w1, sv, KC.pxy, KC.pxy2);
+            // In the packed form the row's filter work runs unguarded: the conditions are uniform,
+            // a row that is not filtered next only wastes work on values nobody reads, and the
+            // straight code schedules better (2048^2 Q2: 0.555 -> 0.505 ms per stage launch)
+            if (PACK || need_v) vertical_jumps(w1, sv, KC.pxy, KC.pxy2);
             horizontal_jumps(w1, w2, sh, KC.pxy, KC.pxy2);
             VG av = z, shc = z;
 #pragma unroll
             for (int l = 0; l <= LMAX; ++l) {
               shc = vmad(sh[l], wy[l], shc);
-              if (need_v) av = vmad(shfl_up_v(sv[l], 1) + sv[l], wx[l], av);
+              if (PACK || need_v) av = vmad(shfl_up_v(sv[l], 1) + sv[l], wx[l], av);
               if (l == 0) {
                 // density: edge-averaged value jumps, J^V / (2 h_x) and the face (t-2 | t-1) / (2 h_y)
                 if ((LIM && a.hybrid) && g == 0) {
@@ -1364,11 +1367,12 @@ struct Stage2D {
               if constexpr (PACK && !OE) {
                 // Q of the pair's two variables in one 64-bit word per lane
                 f2* q2 = (f2*)wq + ((g * LMAX + (l - 1)) << 5) + lane;
-                if (filt_row) {
-                  const f2 x = vfma(shc, f2{by2, by2}, *q2);   // Q of row t-2 + its top face
-                  sig[l] = fmax(fmax(sig[l], x.x), x.y);
-                }
-                if (need_v) *q2 = vfma(shc, f2{by1, by1}, vscale(av, bx1));   // Q of row t-1
+                // Q of row t-2 + its top face (sig is read only when row t-2 is filtered), then Q of
+                // row t-1 (rows are visited in order, so the Q read here is the one written for
+                // row t-2 in the previous iteration)
+                const f2 x = vfma(shc, f2{by2, by2}, *q2);
+                sig[l] = fmax(fmax(sig[l], x.x), x.y);
+                *q2 = vfma(shc, f2{by1, by1}, vscale(av, bx1));
                 continue;
               }
               sfor<GW>([&](auto J_) {
