@@ -999,7 +999,7 @@ struct Stage2D {
         {
           T bot[NQ][NV], top[NQ][NV];
           edge_traces_h(u, bot, top);
-          if (t >= yb - 1) {
+          if (PACK || t >= yb - 1) {   // (packed form: unguarded, see the filter)
             if constexpr (PACK) {
               f2 Fh2[NQ][NV / 2];
 #pragma unroll
@@ -1029,7 +1029,7 @@ struct Stage2D {
               }
             }
             // finalise u~ of row t-1 with its top-face term (P_q(+1) = 1)
-            if (t - 1 >= yb - 1 && t - 1 <= ye) {
+            if (PACK || (t - 1 >= yb - 1 && t - 1 <= ye)) {
               const int s = sl1;
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
@@ -1273,7 +1273,7 @@ struct Stage2D {
         const bool need_v = (t - 1 >= yb && t - 1 < ye);      // row t-1 is filtered next iteration
         T bx1 = T(0), by1 = T(0), invH1 = T(0);
         bool phys1 = true;
-        if (r1) {
+        if (PACK || r1) {
           T ub[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
@@ -1295,7 +1295,7 @@ struct Stage2D {
 #pragma unroll
         for (int l = 0; l <= LMAX; ++l) sig[l] = T(0);
         T eta2 = T(0);                                            // hybrid: eta of row t-2
-        if (a.filter_on && (need_v || filt_row)) {
+        if (a.filter_on && (PACK || need_v || filt_row)) {
           T eta_v = T(0), eta_h = T(0);
           const int s1 = sl1, s2 = sl2;
           // groups of variables (pairs in packed FP32, else one variable): the jumps are linear in
@@ -1348,7 +1348,11 @@ struct Stage2D {
             for (int l = 0; l <= LMAX; ++l) sv[l] = sh[l] = z;
             // In the packed form the row's filter work runs unguarded: the conditions are uniform,
             // a row that is not filtered next only wastes work on values nobody reads, and the
-            // straight code schedules better (2048^2 Q2: 0.555 -> 0.505 ms per stage launch)
+            // straight code schedules better (2048^2 Q2: 0.555 -> 0.505 ms per stage launch; the
+            // horizontal face, the top-face update of row t-1 and its average parameters likewise,
+            // whose guards fail only in the first iteration: -> 0.482 ms. Those writes go to a row
+            // slot that the partial stage value of row yb overwrites before it is read. Unguarding
+            // the partial stage value itself as well was slower, 0.497 ms)
             if (PACK || need_v) vertical_jumps(w1, sv, KC.pxy, KC.pxy2);
             horizontal_jumps(w1, w2, sh, KC.pxy, KC.pxy2);
             VG av = z, shc = z;
