@@ -104,3 +104,32 @@ def test_splitmix64_reference_stream():
     h = I.SplitMix64(0)
     v = h.block_u64(2)
     assert int(v[0]) == 0xE220A8397B1DCDAF and int(v[1]) == 0x6E789E6AA1B965F4
+
+
+def test_batch_and_probe_argument_checks_need_no_gpu(lib):
+    """The batched entry points and the bounded-wait probe reject bad arguments before touching the
+    device."""
+    n = N.load()
+    arr = (ctypes.c_void_p * 1)(None)
+    assert n.dg_batch_run(None, 1, 1) == -1
+    assert n.dg_batch_run_persistent(None, 1, 1) == -1
+    assert n.dg_batch_run_persistent(arr, 0, 1) == -1
+    assert n.dg_batch_run_persistent(arr, 1, -1) == -1
+    assert n.dg_batch_run_persistent(arr, 1, 1) == -1        # a NULL solver
+    status, ms = ctypes.c_uint(0), ctypes.c_double(0.0)
+    assert n.dg_probe_wait_timeout(1 << 25, ctypes.byref(status), ctypes.byref(ms)) == -1
+    assert n.dg_probe_wait_timeout(10, None, ctypes.byref(ms)) == -1
+
+
+def test_build_compiles_every_instantiation_unit():
+    """The 2D stage kernel's (form, degree) objects and the batched kernels' per-degree objects are all
+    in the build, each with its own defines, next to the dispatch object."""
+    objs = {o: defs for _, o, defs in B.UNITS}
+    for f in range(5):
+        for k in (1, 2, 3):
+            assert objs["stage2d_f%d_k%d.o" % (f, k)] == ["-DS2_FORM=%d" % f, "-DS2_K=%d" % k]
+    assert objs["stage2d_dispatch.o"] == ["-DS2_DISPATCH"]
+    for k in (1, 2, 3):
+        assert objs["dg_batch_k%d.o" % k] == ["-DDG_BATCH_K=%d" % k]
+    assert objs["dg_batch.o"] == [] and objs["dg_api.o"] == []
+    assert len(objs) == len(B.UNITS)                       # no object built twice
