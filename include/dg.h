@@ -221,6 +221,9 @@ DG_API dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps)
  * bounded number of times (about a second); if one gives up, all warps leave and the call returns
  * DG_ERR_TIMEOUT with the solvers' states undefined (a wait that is not broken lasts at most one
  * stage of its solver). Allocates a small device scratch block (16 bytes per solver) per call.
+ * A class's launch runs until its whole queue (steps x 3 x its items) is taken, even after all its
+ * solvers have reached their T_end: their items are then skipped, at about a microsecond of a warp
+ * each, so pass a step count near the one needed (dg_batch_run idles the same way, per step).
  * Synchronises; DG_ERR_NONPHYSICAL as dg_batch_run. Not while a stream is captured. */
 DG_API dg_status dg_batch_run_persistent(dg_solver* const* solvers, int n, long long steps);
 
