@@ -224,6 +224,7 @@ DG_API dg_status dg_batch_run(dg_solver* const* solvers, int n, long long steps)
  * A class's launch runs until its whole queue (steps x 3 x its items) is taken, even after all its
  * solvers have reached their T_end: their items are then skipped, at about a microsecond of a warp
  * each, so pass a step count near the one needed (dg_batch_run idles the same way, per step).
+ * steps above 2^30 are rejected with DG_ERR_ARG (the per-solver stage counters are 32-bit).
  * Synchronises; DG_ERR_NONPHYSICAL as dg_batch_run. Not while a stream is captured. */
 DG_API dg_status dg_batch_run_persistent(dg_solver* const* solvers, int n, long long steps);
 

@@ -608,6 +608,7 @@ using namespace dgk;
 
 static dg_status batch_run(dg_solver* const* solvers, int n, long long steps, bool persistent) {
   if (!solvers || n < 1 || steps < 0) return DG_ERR_ARG;
+  if (persistent && steps > (1LL << 30)) return DG_ERR_ARG;   // the stage counters are 32-bit
   int dev0 = -1;
   for (int i = 0; i < n; ++i) {
     const dg_solver* s = solvers[i];

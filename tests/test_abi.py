@@ -116,6 +116,7 @@ def test_batch_and_probe_argument_checks_need_no_gpu(lib):
     assert n.dg_batch_run_persistent(arr, 0, 1) == -1
     assert n.dg_batch_run_persistent(arr, 1, -1) == -1
     assert n.dg_batch_run_persistent(arr, 1, 1) == -1        # a NULL solver
+    assert n.dg_batch_run_persistent(arr, 1, (1 << 30) + 1) == -1   # beyond the 32-bit stage counters
     status, ms = ctypes.c_uint(0), ctypes.c_double(0.0)
     assert n.dg_probe_wait_timeout(1 << 25, ctypes.byref(status), ctypes.byref(ms)) == -1
     assert n.dg_probe_wait_timeout(10, None, ctypes.byref(ms)) == -1
